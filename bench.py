@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark: TV-regularised cone-beam CT reconstruction (Algorithm A1 with the
+coarse-to-fine multigrid schedule) at paper scale on GB300.
+
+One step = one full reconstruction of the paper-scale workload: a
+256x256x128 volume at 1 mm, 40 views over 360 degrees on a 512x384 detector
+at 0.78 mm (SAD 1000 mm, SDD 1500 mm), a seeded head-and-neck-like ellipsoid
+phantom with Poisson noise at 5e4 photons per ray, 3 multigrid levels
+(64 -> 128 -> 256 in-plane), 40/30/30 FBS iterations, step 1/L from 20 power
+iterations per level, lambda 0.05. The metric is seconds per reconstruction
+(lower is better); with N GPUs every rank reconstructs its own scan (weak
+scaling, no data-path collective) and the value is the job's time per scan.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on this machine's host cores (a
+bounded sample, scaled to one reconstruction).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128
+METRIC = "recon sec at 256x256x128 x 40 views (paper-scale workload)"
+WORKLOAD = ("paper-scale: 256x256x128 voxels @1 mm, 40 views/360 deg, 512x384 detector @0.78 mm, "
+            "SAD 1000 / SDD 1500 mm, head-and-neck-like ellipsoid phantom, Poisson 5e4 photons/ray, "
+            "3-level multigrid, 40/30/30 FBS iterations, tau = 1/L (20 power iterations per level), "
+            "lambda 0.05, eps_tv 1e-5, Armijo c 0.01 alpha 0.6 tol 0.1%")
+PAPER_CONTEXT = {"seconds": 130.3, "hardware": "NVIDIA Tesla C1060",
+                 "workload": "NCAT 512x512x70, 40 views, 512x384 imager, 4-level multigrid",
+                 "source": "Table 1"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, y):
+    """Seconds per reconstruction of the FP64 oracle, from a bounded sample:
+    P and P^T over a subset of views and one ROF solve at every multigrid
+    level, scaled by the schedule's operation counts."""
+    import numpy as np
+    from oracle import oracle as orc
+    g = orc.Geometry.from_workload(wl)
+    levels = len(wl.iters)
+    t_total = 0.0
+    rng = np.random.default_rng(0)
+    parts = []
+    for lev in range(levels):
+        gl = g.coarse(2 ** (levels - 1 - lev)) if lev < levels - 1 else g
+        nsub = 1
+        sub = orc.Geometry(gl.nx, gl.ny, gl.nz, gl.dx, gl.dy, gl.dz, gl.nu, gl.nv, gl.du, gl.dv, gl.sad, gl.sdd,
+                           gl.angles[:nsub].copy(), gl.step_ratio)
+        f = rng.random(gl.vol_shape) * 0.02
+        t0 = time.perf_counter()
+        p = orc.forward_project(sub, f)
+        t1 = time.perf_counter()
+        orc.back_project(sub, p)
+        t2 = time.perf_counter()
+        gaux = f + 0.001 * rng.standard_normal(gl.vol_shape)
+        orc.rof_solve(gl, gaux, wl.lam, 1e-5, orc.TVParams(eps_tv=1e-5))
+        t3 = time.perf_counter()
+        scale = gl.n_views / nsub
+        tp, tpt, trof = (t1 - t0) * scale, (t2 - t1) * scale, t3 - t2
+        n_fbs = wl.iters[lev]
+        n_pow = 20
+        t_total += n_fbs * (tp + tpt + trof) + n_pow * (tp + tpt)
+        parts.append(f"level {lev}: P,P^T on {nsub}/{gl.n_views} views x{scale:.0f}, one ROF solve")
+    return t_total, "; ".join(parts)
+
+
+def cpu_cores():
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count())
+    except ValueError:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+    from paper_1001_0599_gb300 import synthetic
+    orc.build()
+    wl = synthetic.workload("paper")
+    _, y = synthetic.make_problem(wl)
+    times = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        t, sample = oracle_sample(wl, y)
+        if i >= args.warmup:
+            times.append(t)
+    v = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_1001_0599_gb300 import build as lib_build
+    lib_build.build()
+    from paper_1001_0599_gb300 import cbct, synthetic
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    wl = synthetic.workload("paper")
+    truth, y = synthetic.make_problem(wl)
+    if world > 1:  # each rank reconstructs its own scan (different noise draw)
+        y = synthetic.poisson_log_sinogram(synthetic.exact_sinogram(synthetic.make_phantom(wl), wl),
+                                           wl.photons, wl.noise_seed + 1000 * rank)
+    g = cbct.geometry_from_workload(wl)
+    tv = cbct.TvParams.paper(eps_tv=1e-5)
+    params = cbct.make_recon_params(wl.lam, wl.iters, tv, power_iters=20, clamp=True)
+    ws = cbct.workspace(cbct.cbct_workspace_size(g, params))
+    stats = cbct.stats_buffer()
+    d_y = torch.from_numpy(y.astype(np.float32)).cuda()
+    vol = torch.zeros(g.vol_shape, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        cbct.cbct_reconstruct(g, d_y, vol, params, ws, stats)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    cbct.cbct_profile_reset()
+    cbct.cbct_profile_enable(True)
+    n0 = cbct.cbct_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        cbct.cbct_profile_collect()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = cbct.cbct_launch_count() - n0 - 0
+    cbct.cbct_profile_enable(False)
+    prof = cbct.cbct_profile_query()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    sec_per_scan = total_ms / 1e3 / (args.steps * world)
+    st = cbct.read_stats(stats)
+    recon = vol.cpu().numpy().astype(np.float64)
+    rel_err = float(np.linalg.norm(recon - truth) / np.linalg.norm(truth))
+    corr = float(np.corrcoef(recon.ravel(), truth.ravel())[0, 1])
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    e2e = None
+    if not args.no_e2e:
+        h_y = torch.from_numpy(y.astype(np.float32)).pin_memory()
+        h_vol = torch.empty(g.vol_shape, dtype=torch.float32).pin_memory()
+        ws_h = cbct.workspace(cbct.cbct_workspace_size_host(g, params))
+        for _ in range(max(1, args.warmup)):
+            cbct.cbct_reconstruct_host(g, h_y.numpy(), h_vol.numpy(), params, ws_h)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            cbct.cbct_reconstruct_host(g, h_y.numpy(), h_vol.numpy(), params, ws_h)
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": e2e_s / (args.steps * world), "unit": "s",
+               "h2d_bytes_per_step": int(h_y.numel() * 4), "d2h_bytes_per_step": int(h_vol.numel() * 4)}
+        del ws_h
+
+    # roofline of the dominant kernel
+    roof = roofline(prof, wl, args.steps, clocks)
+    peaks = measured_peaks()
+    line = {"metric": METRIC, "value": sec_per_scan, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "reductions": "FP64 across blocks, compensated FP32 within"},
+            "clocks": clocks, "gpu_launches": int(launches), "roofline": roof,
+            "e2e": e2e,
+            "kernels": {k: {"launches": n // max(args.steps, 1), "ms_per_step": ms / max(args.steps, 1)}
+                        for k, (n, ms) in prof.items() if n},
+            "quality": {"rel_error_vs_phantom": rel_err, "correlation": corr, "flags": int(st.flags),
+                        "status": int(st.status), "taus": [float(st.tau[i]) for i in range(3)]},
+            "paper_context": PAPER_CONTEXT,
+            "peaks_source": peaks.get("_source")}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        orc.build()
+        v, sample = oracle_sample(wl, y)
+        line["cpu_baseline"] = {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": sample + " (scaled to one reconstruction)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        d["_source"] = "measured (MEASURED_PEAKS.json)"
+        return d
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "_source": "fallback"}
+
+
+def roofline(prof, wl, steps, clocks):
+    """Dominant kernel by device time. Projector kernels are bound by FP32
+    issue (no dense contraction, working set in L2): algorithmic work is
+    2 flops per non-zero weight of P, nnz per level from tests/golden/nnz.json;
+    peak = SMs x 128 FP32 lanes x 2 flops x max SM clock."""
+    import torch
+    name, (n, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    if n == 0 or ms <= 0:
+        return None
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "nnz.json")) as fh:
+            nnz = json.load(fh)["paper"]
+    except (OSError, KeyError, ValueError):
+        nnz = None
+    levels = len(wl.iters)
+    if name in ("back_project_step", "forward_residual", "back_project", "forward_project") and nnz:
+        # launches per reconstruction at each level (coarse -> fine)
+        flops = 0.0
+        for lev in range(levels):
+            gl = levels - 1 - lev
+            per = wl.iters[lev] if name in ("back_project_step", "forward_residual") else 20
+            flops += per * 2.0 * float(nnz[str(gl)])
+        flops *= steps
+        achieved = flops / (ms / 1e3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "work": "2 flops per non-zero sample-voxel weight of P (nnz from the oracle's count)",
+                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
+                "avg_launch_ms": ms / n}
+    # TV sweeps: HBM-bound (report time only; bytes depend on the sweep count)
+    return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+            "frac": None, "traffic": None, "avg_launch_ms": ms / n}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

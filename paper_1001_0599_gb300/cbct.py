@@ -1,0 +1,378 @@
+"""Python binding of libcbct (include/cbct.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and forwards
+device pointers (torch CUDA tensors), sizes and the current CUDA stream; all
+computation runs in the library's CUDA kernels. There is no CPU fallback:
+importing this module on a machine without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcbct.so")
+
+CBCT_MAX_LEVELS = 4
+CBCT_MAX_ITERS = 512
+CBCT_MAX_STEP_LOG = 8192
+
+STATUS = {0: "CBCT_OK", 1: "CBCT_ERR_INVALID_ARG", 2: "CBCT_ERR_CUDA", 3: "CBCT_ERR_OUT_OF_MEMORY",
+          4: "CBCT_ERR_WORKSPACE_TOO_SMALL", 5: "CBCT_ERR_NOT_CONVERGED", 6: "CBCT_ERR_UNSUPPORTED",
+          7: "CBCT_ERR_TIMEOUT"}
+
+
+class CbctError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GeometryDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("nu", ctypes.c_int), ("nv", ctypes.c_int),
+                ("du", ctypes.c_double), ("dv", ctypes.c_double),
+                ("sad", ctypes.c_double), ("sdd", ctypes.c_double),
+                ("n_views", ctypes.c_int), ("angles", ctypes.POINTER(ctypes.c_double)),
+                ("step_ratio", ctypes.c_double)]
+
+
+class TvParams(ctypes.Structure):
+    _fields_ = [("eps_tv", ctypes.c_double), ("c", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("rel_tol", ctypes.c_double), ("max_inner", ctypes.c_int),
+                ("max_backtracks", ctypes.c_int), ("s0", ctypes.c_double)]
+
+    @classmethod
+    def paper(cls, eps_tv: float = 1e-5, max_inner: int = 50, max_backtracks: int = 40, s0: float = 0.0):
+        """Sec. II.B constants: c = 0.01, alpha = 0.6, relative tolerance 0.1 %."""
+        return cls(eps_tv, 0.01, 0.6, 1e-3, max_inner, max_backtracks, s0)
+
+
+class TvStats(ctypes.Structure):
+    _fields_ = [("n_inner", ctypes.c_int), ("backtracks", ctypes.c_int), ("flags", ctypes.c_int),
+                ("status", ctypes.c_int), ("e_first", ctypes.c_double), ("e_last", ctypes.c_double)]
+
+
+class ReconParams(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("n_levels", ctypes.c_int),
+                ("iters", ctypes.c_int * CBCT_MAX_LEVELS), ("tau", ctypes.c_double * CBCT_MAX_LEVELS),
+                ("power_iters", ctypes.c_int), ("clamp", ctypes.c_int), ("tv", TvParams),
+                ("replay", ctypes.POINTER(ctypes.c_int32)), ("replay_len", ctypes.c_int)]
+
+
+class IterStats(ctypes.Structure):
+    _fields_ = [("e2", ctypes.c_double), ("e_rof_first", ctypes.c_double), ("e_rof_last", ctypes.c_double),
+                ("level", ctypes.c_int), ("n_inner", ctypes.c_int), ("backtracks", ctypes.c_int),
+                ("flags", ctypes.c_int)]
+
+
+class ReconStats(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double * CBCT_MAX_LEVELS), ("lipschitz", ctypes.c_double * CBCT_MAX_LEVELS),
+                ("n_iters", ctypes.c_int), ("flags", ctypes.c_int), ("status", ctypes.c_int),
+                ("n_steps", ctypes.c_int), ("iters", IterStats * CBCT_MAX_ITERS),
+                ("steps", ctypes.c_int32 * CBCT_MAX_STEP_LOG)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load() -> ctypes.CDLL:
+    """Load libcbct.so (built in-tree by build.py). Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libcbct.so not built at {LIB_PATH}; run paper_1001_0599_gb300/build.py")
+    L = ctypes.CDLL(LIB_PATH)
+    st = ctypes.c_int
+    L.cbct_geometry_create.argtypes = [ctypes.POINTER(GeometryDesc), ctypes.POINTER(_P)]
+    L.cbct_geometry_create.restype = st
+    L.cbct_geometry_destroy.argtypes = [_P]
+    L.cbct_geometry_destroy.restype = None
+    L.cbct_geometry_level_dims.argtypes = [_P, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
+    L.cbct_geometry_level_dims.restype = st
+    L.cbct_forward_project.argtypes = [_P, _P, _P, _P]
+    L.cbct_forward_project.restype = st
+    L.cbct_residual.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
+    L.cbct_residual.restype = st
+    L.cbct_back_project.argtypes = [_P, _P, _P, _P]
+    L.cbct_back_project.restype = st
+    L.cbct_gradient_step.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
+    L.cbct_gradient_step.restype = st
+    d = ctypes.c_double
+    L.cbct_tv_energy_grad.argtypes = [_P, _P, _P, d, d, d, _P, _P, _P, ctypes.c_size_t, _P]
+    L.cbct_tv_energy_grad.restype = st
+    L.cbct_tv_trial.argtypes = [_P, _P, _P, _P, d, d, d, d, _P, _P, ctypes.c_size_t, _P]
+    L.cbct_tv_trial.restype = st
+    L.cbct_tv_denoise.argtypes = [_P, _P, _P, d, d, ctypes.POINTER(TvParams), _P, ctypes.c_size_t, _P, _P]
+    L.cbct_tv_denoise.restype = st
+    L.cbct_prolongate.argtypes = [ctypes.c_int] * 3 + [_P, _P, _P]
+    L.cbct_prolongate.restype = st
+    L.cbct_power_lipschitz.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_size_t, _P]
+    L.cbct_power_lipschitz.restype = st
+    L.cbct_workspace_size.argtypes = [_P, ctypes.POINTER(ReconParams), ctypes.POINTER(ctypes.c_size_t)]
+    L.cbct_workspace_size.restype = st
+    L.cbct_workspace_size_host.argtypes = [_P, ctypes.POINTER(ReconParams), ctypes.POINTER(ctypes.c_size_t)]
+    L.cbct_workspace_size_host.restype = st
+    L.cbct_reconstruct.argtypes = [_P, _P, _P, ctypes.POINTER(ReconParams), _P, ctypes.c_size_t, _P, _P]
+    L.cbct_reconstruct.restype = st
+    L.cbct_reconstruct_host.argtypes = [_P, _P, _P, ctypes.POINTER(ReconParams), _P, ctypes.c_size_t,
+                                        ctypes.POINTER(ReconStats), _P]
+    L.cbct_reconstruct_host.restype = st
+    L.cbct_last_error.argtypes = []
+    L.cbct_last_error.restype = ctypes.c_char_p
+    L.cbct_launch_count.argtypes = []
+    L.cbct_launch_count.restype = ctypes.c_int64
+    L.cbct_profile_enable.argtypes = [ctypes.c_int]
+    L.cbct_profile_enable.restype = st
+    L.cbct_profile_collect.argtypes = []
+    L.cbct_profile_collect.restype = st
+    L.cbct_profile_kernels.argtypes = []
+    L.cbct_profile_kernels.restype = ctypes.c_int
+    L.cbct_profile_name.argtypes = [ctypes.c_int]
+    L.cbct_profile_name.restype = ctypes.c_char_p
+    L.cbct_profile_query.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+    L.cbct_profile_query.restype = st
+    L.cbct_profile_reset.argtypes = []
+    L.cbct_profile_reset.restype = None
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise CbctError(status, load().cbct_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev(t, name: str, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    return t.data_ptr()
+
+
+def _f32(t, name):
+    import torch
+    return _dev(t, name, torch.float32)
+
+
+def _f64(t, name):
+    import torch
+    return _dev(t, name, torch.float64)
+
+
+class Geometry:
+    """Owning wrapper of a cbct_geometry handle."""
+
+    def __init__(self, handle: int, desc: GeometryDesc, angles: np.ndarray):
+        self.handle = handle
+        self.desc = desc
+        self.angles = angles
+
+    @property
+    def vol_shape(self):
+        return (self.desc.nx, self.desc.ny, self.desc.nz)
+
+    @property
+    def sino_shape(self):
+        return (self.desc.n_views, self.desc.nv, self.desc.nu)
+
+    def level_dims(self, level: int):
+        return cbct_geometry_level_dims(self, level)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.cbct_geometry_destroy(self.handle)
+            self.handle = None
+
+
+def cbct_geometry_create(nx, ny, nz, dx, dy, dz, nu, nv, du, dv, sad, sdd, angles,
+                         step_ratio: float = 0.5) -> Geometry:
+    L = load()
+    ang = np.ascontiguousarray(angles, dtype=np.float64)
+    desc = GeometryDesc(nx, ny, nz, dx, dy, dz, nu, nv, du, dv, sad, sdd, len(ang),
+                        ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), step_ratio)
+    h = _P()
+    _check(L.cbct_geometry_create(ctypes.byref(desc), ctypes.byref(h)))
+    return Geometry(h.value, desc, ang)
+
+
+def geometry_from_workload(wl) -> Geometry:
+    return cbct_geometry_create(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz, wl.nu, wl.nv, wl.du, wl.dv,
+                                wl.sad, wl.sdd, wl.angles, wl.step_ratio)
+
+
+def cbct_geometry_level_dims(geom: Geometry, level: int):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().cbct_geometry_level_dims(geom.handle, level, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def cbct_forward_project(geom: Geometry, vol, sino, stream=None) -> None:
+    _check(load().cbct_forward_project(geom.handle, _f32(vol, "vol"), _f32(sino, "sino"), _stream(stream)))
+
+
+def cbct_residual(geom: Geometry, vol, y, r, sumsq, ws, stream=None) -> None:
+    _check(load().cbct_residual(geom.handle, _f32(vol, "vol"), _f32(y, "y"), _f32(r, "r"),
+                                _f64(sumsq, "sumsq"), _dev(ws, "ws"), ws.numel() * ws.element_size(),
+                                _stream(stream)))
+
+
+def cbct_back_project(geom: Geometry, sino, vol, stream=None) -> None:
+    _check(load().cbct_back_project(geom.handle, _f32(sino, "sino"), _f32(vol, "vol"), _stream(stream)))
+
+
+def cbct_gradient_step(geom: Geometry, r, f, g, scale: float, stream=None) -> None:
+    _check(load().cbct_gradient_step(geom.handle, _f32(r, "r"), _f32(f, "f"), _f32(g, "g"), float(scale),
+                                     _stream(stream)))
+
+
+def cbct_tv_energy_grad(geom: Geometry, f, g, lam, tau, eps_tv, d, out, ws, stream=None) -> None:
+    _check(load().cbct_tv_energy_grad(geom.handle, _f32(f, "f"), _f32(g, "g"), lam, tau, eps_tv, _f32(d, "d"),
+                                      _f64(out, "out"), _dev(ws, "ws"), ws.numel() * ws.element_size(),
+                                      _stream(stream)))
+
+
+def cbct_tv_trial(geom: Geometry, f, d, g, s, lam, tau, eps_tv, out, ws, stream=None) -> None:
+    _check(load().cbct_tv_trial(geom.handle, _f32(f, "f"), _f32(d, "d"), _f32(g, "g"), s, lam, tau, eps_tv,
+                                _f64(out, "out"), _dev(ws, "ws"), ws.numel() * ws.element_size(),
+                                _stream(stream)))
+
+
+def cbct_tv_denoise(geom: Geometry, g, f, lam, tau, params: TvParams, ws, stats=None, stream=None) -> None:
+    _check(load().cbct_tv_denoise(geom.handle, _f32(g, "g"), _f32(f, "f"), lam, tau, ctypes.byref(params),
+                                  _dev(ws, "ws"), ws.numel() * ws.element_size(),
+                                  _dev(stats, "stats"), _stream(stream)))
+
+
+def cbct_prolongate(coarse, fine, stream=None) -> None:
+    ncx, ncy, ncz = coarse.shape
+    assert tuple(fine.shape) == (2 * ncx, 2 * ncy, 2 * ncz)
+    _check(load().cbct_prolongate(ncx, ncy, ncz, _f32(coarse, "coarse"), _f32(fine, "fine"), _stream(stream)))
+
+
+def cbct_power_lipschitz(geom: Geometry, level: int, n_iter: int, out, ws, stream=None) -> None:
+    _check(load().cbct_power_lipschitz(geom.handle, level, n_iter, _f64(out, "out"), _dev(ws, "ws"),
+                                       ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def make_recon_params(lam: float, iters: Sequence[int], tv: Optional[TvParams] = None,
+                      taus: Optional[Sequence[float]] = None, power_iters: int = 20, clamp: bool = True,
+                      replay: Optional[Sequence[Sequence[int]]] = None) -> ReconParams:
+    """ReconParams; ``replay`` is a list of per-iteration step-reduction lists."""
+    p = ReconParams()
+    p.lambda_ = lam
+    p.n_levels = len(iters)
+    for i, n in enumerate(iters):
+        p.iters[i] = int(n)
+        p.tau[i] = float(taus[i]) if taus is not None else 0.0
+    p.power_iters = power_iters
+    p.clamp = 1 if clamp else 0
+    p.tv = tv if tv is not None else TvParams.paper()
+    if replay is not None:
+        flat = []
+        for steps in replay:
+            flat.append(len(steps))
+            flat.extend(int(s) for s in steps)
+        arr = np.ascontiguousarray(flat, dtype=np.int32)
+        p._replay_keep = arr
+        p.replay = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        p.replay_len = len(arr)
+    return p
+
+
+def cbct_workspace_size(geom: Geometry, params: Optional[ReconParams] = None) -> int:
+    n = ctypes.c_size_t()
+    _check(load().cbct_workspace_size(geom.handle, ctypes.byref(params) if params is not None else None,
+                                      ctypes.byref(n)))
+    return n.value
+
+
+def cbct_workspace_size_host(geom: Geometry, params: Optional[ReconParams] = None) -> int:
+    n = ctypes.c_size_t()
+    _check(load().cbct_workspace_size_host(geom.handle, ctypes.byref(params) if params is not None else None,
+                                           ctypes.byref(n)))
+    return n.value
+
+
+def workspace(nbytes: int, device=None):
+    """A 256-byte aligned device buffer of ``nbytes`` (torch allocations are)."""
+    import torch
+    return torch.empty(int(nbytes), dtype=torch.uint8, device=device or "cuda")
+
+
+def stats_buffer(kind=ReconStats, device=None):
+    import torch
+    return torch.zeros(ctypes.sizeof(kind), dtype=torch.uint8, device=device or "cuda")
+
+
+def read_stats(buf, kind=ReconStats):
+    host = buf.cpu().numpy().tobytes()
+    return kind.from_buffer_copy(host)
+
+
+def cbct_reconstruct(geom: Geometry, sino, vol, params: ReconParams, ws, stats=None, stream=None) -> None:
+    _check(load().cbct_reconstruct(geom.handle, _f32(sino, "sino"), _f32(vol, "vol"), ctypes.byref(params),
+                                   _dev(ws, "ws"), ws.numel() * ws.element_size(), _dev(stats, "stats"),
+                                   _stream(stream)))
+
+
+def cbct_reconstruct_host(geom: Geometry, h_sino: np.ndarray, h_vol: np.ndarray, params: ReconParams, ws,
+                          stream=None) -> ReconStats:
+    """Host buffers in and out (pinned host tensors' numpy views are fine)."""
+    for a, name in ((h_sino, "h_sino"), (h_vol, "h_vol")):
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            raise TypeError(f"{name} must be a contiguous float32 host array")
+    st = ReconStats()
+    _check(load().cbct_reconstruct_host(geom.handle, h_sino.ctypes.data, h_vol.ctypes.data, ctypes.byref(params),
+                                        _dev(ws, "ws"), ws.numel() * ws.element_size(), ctypes.byref(st),
+                                        _stream(stream)))
+    return st
+
+
+def cbct_last_error() -> str:
+    return load().cbct_last_error().decode()
+
+
+def cbct_launch_count() -> int:
+    return int(load().cbct_launch_count())
+
+
+def cbct_profile_enable(on: bool = True) -> None:
+    _check(load().cbct_profile_enable(1 if on else 0))
+
+
+def cbct_profile_collect() -> None:
+    _check(load().cbct_profile_collect())
+
+
+def cbct_profile_reset() -> None:
+    load().cbct_profile_reset()
+
+
+def cbct_profile_query() -> dict:
+    L = load()
+    out = {}
+    for k in range(L.cbct_profile_kernels()):
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        _check(L.cbct_profile_query(k, ctypes.byref(n), ctypes.byref(ms)))
+        out[L.cbct_profile_name(k).decode()] = (int(n.value), float(ms.value))
+    return out

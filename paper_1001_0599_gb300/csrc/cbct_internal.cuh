@@ -1,0 +1,245 @@
+// Internal definitions shared by the libcbct translation units (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cbct.h"
+
+namespace cbct {
+
+// ---------------------------------------------------------------------------
+// Geometry as the kernels see it
+// ---------------------------------------------------------------------------
+
+// One in-plane ray line (view, iu), derived in FP64 on the host. Sample j of
+// the line (k = kc + j in the paper's discretisation of Eq. 1, in-plane
+// distance rho_k = k drho from the source) sits at
+//     t = j drho - delta,   (x, y) = (mx, my) + t (ex, ey),
+//     z(iv) = rho_k v(iv) / L_xy.
+// (mx, my) is the point of the line closest to the rotation axis, so x, y
+// stay small and keep FP32 precision.
+struct RayCol {
+    float mx, my;     // closest point of the line to the axis, mm
+    float ex, ey;     // unit in-plane direction
+    float delta;      // rho_c - kc drho, rho_c = in-plane distance source -> (mx, my)
+    float inv_lxy;    // 1 / L_xy(u), L_xy = in-plane source-pixel distance
+    int kc;           // sample index nearest (mx, my)
+    int16_t jlo, jhi; // samples kc+jlo .. kc+jhi cover the volume's support (empty if jlo > jhi)
+};
+static_assert(sizeof(RayCol) == 32, "RayCol must stay 32 bytes");
+
+struct VolGeom {
+    int nx, ny, nz;
+    float dx, dy, dz;
+    float inv_dx, inv_dy, inv_dz;
+    float cx, cy, cz;          // (n - 1) / 2
+    float drho;                // in-plane sample spacing
+    const RayCol *cols;        // [n_views][nu]
+};
+
+struct DetGeom {
+    int nu, nv, n_views;
+    float du, dv, inv_du, inv_dv, cu, cv;
+    float sad, sdd;
+    const float2 *views;       // (cos, sin) per view
+};
+
+// Continuous voxel coordinates of sample j of a ray line (shared by the
+// projector and its transpose so both see identical sample positions).
+__device__ __forceinline__ void sample_xy(const VolGeom &g, const RayCol &rc, int j, float &fx,
+                                          float &fy)
+{
+    float t = __fmaf_rn((float)j, g.drho, -rc.delta);
+    float x = __fmaf_rn(t, rc.ex, rc.mx);
+    float y = __fmaf_rn(t, rc.ey, rc.my);
+    fx = __fmaf_rn(x, g.inv_dx, g.cx);
+    fy = __fmaf_rn(y, g.inv_dy, g.cy);
+}
+
+__device__ __forceinline__ float sample_rho(const VolGeom &g, const RayCol &rc, int j)
+{
+    return __fmul_rn((float)(rc.kc + j), g.drho);
+}
+
+// ---------------------------------------------------------------------------
+// Compensated FP32 ("double-float") accumulation for the reduction trees:
+// GB300's FP64 rate is a small fraction of FP32, so per-thread and per-warp
+// partial sums are carried as exact (hi, lo) float pairs and converted to
+// FP64 only where blocks are combined.
+// ---------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
+
+__device__ __forceinline__ DF df_add(DF a, float b)
+{
+    float s = __fadd_rn(a.hi, b);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    e = __fadd_rn(e, a.lo);
+    float hi = __fadd_rn(s, e);
+    float lo = __fsub_rn(e, __fsub_rn(hi, s));
+    return DF{hi, lo};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    float s = __fadd_rn(a.hi, b.hi);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    float hi = __fadd_rn(s, e);
+    float lo = __fsub_rn(e, __fsub_rn(hi, s));
+    return DF{hi, lo};
+}
+
+__device__ __forceinline__ DF df_warp_sum(DF v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DF w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, w);
+    }
+    return v;
+}
+
+// Block-wide sum of K double-float values per thread; thread 0 receives the
+// FP64 totals in out[]. Deterministic order. scratch: >= 32*K doubles smem.
+template <int K>
+__device__ __forceinline__ void block_sum_df(DF (&v)[K], double *scratch, double (&out)[K])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = df_warp_sum(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) scratch[warp * K + k] = (double)v[k].hi + (double)v[k].lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double s = 0.0;
+            for (int w = 0; w < nwarp; w++) s += scratch[w * K + k];
+            out[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Device state shared by the kernels of one call (lives in the workspace)
+// ---------------------------------------------------------------------------
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    int error;        // set when a bounded wait gave up
+    int pad;
+};
+
+struct DevState {
+    GridBarrier bar;
+    double tau;          // current level's step
+    double scale;        // tau * kappa
+    double lipschitz;
+    double vnorm2;       // power iteration: |v|^2 of the current iterate
+    double inv_wnorm;    // power iteration: 1/|w|
+    double e2;           // last data term
+    double red[8];       // results of the last grid-wide reduction
+    int rof_inner;
+    int rof_bt;
+    int rof_flags;
+    int rof_done;
+    int step_log_pos;    // next free entry of the recon step log
+    int iter_pos;        // next iteration record
+    int pad[2];
+};
+
+// ---------------------------------------------------------------------------
+// Launch bookkeeping (profiling + launch count), defined in api.cu
+// ---------------------------------------------------------------------------
+enum KernelId {
+    K_FP = 0,
+    K_FP_RESID,
+    K_BP,
+    K_BP_STEP,
+    K_ROF,
+    K_REDUCE,
+    K_PROLONG,
+    K_FILL,
+    K_MISC,
+    K_COUNT
+};
+
+void launch_begin(int kernel, cudaStream_t s);
+void launch_end(int kernel, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (one per translation unit)
+// ---------------------------------------------------------------------------
+
+// forward projector. mode 0: out = scale * P vol (scale from d_scale if given)
+// mode 1: out = P vol - y (unscaled residual), partials <- sum r^2
+// mode 2: out = ds * (P vol - y) (residual pre-weighted for the transpose), partials <- sum r^2
+int fp_grid_blocks(const DetGeom &d);
+cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
+                           float *out, const double *d_scale, double *partials, int mode,
+                           cudaStream_t s);
+
+// transpose. mode 0: out = P^T sino; mode 1: out = f - scale P^T sino with
+// scale = *d_scale if given, else scale_val (sino pre-weighted by ds when
+// prescaled != 0); mode 2: out = kappa P^T sino with partials <- sum out^2
+// (power iteration)
+int bp_grid_blocks(const VolGeom &v);
+size_t bp_smem_bytes(const VolGeom &v, const DetGeom &d);
+cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, const float *f,
+                        float *out, const double *d_scale, double scale_val, double kappa,
+                        double *partials, int mode, int prescaled, cudaStream_t s);
+
+// small kernels (misc.cu)
+cudaError_t launch_sum_partials(const double *partials, int n, int stride, int k, double *out,
+                                cudaStream_t s);
+cudaError_t launch_e2(const double *partials, int n, double inv_m, DevState *st, cudaStream_t s);
+cudaError_t launch_power_init(DevState *st, double nvox, cudaStream_t s);
+cudaError_t launch_power_update(DevState *st, const double *partials, int n, double kappa_unused,
+                                int first, int last, double *d_L_out, cudaStream_t s);
+cudaError_t launch_set_tau(DevState *st, double tau_given, double kappa, cbct_recon_stats *rs,
+                           int level, cudaStream_t s);
+cudaError_t launch_state_init(DevState *st, cbct_recon_stats *rs, cudaStream_t s);
+cudaError_t launch_fill(float *p, size_t n, float value, cudaStream_t s);
+cudaError_t launch_prolong(int ncx, int ncy, int ncz, const float *c, float *f, cudaStream_t s);
+
+// ROF persistent kernel (tv.cu)
+struct RofArgs {
+    const float *g;       // auxiliary image g (read only)
+    float *f;             // iterate (in/out)
+    float *d;             // gradient workspace
+    double *partials;     // [grid][4]
+    DevState *st;
+    cbct_tv_stats *tv_stats;           // optional
+    cbct_recon_stats *recon_stats;     // optional: append steps + iteration record
+    const int32_t *replay;             // optional: n, m_1..m_n
+    int nx, ny, nz;
+    float inv_dx, inv_dy, inv_dz;
+    double lambda, tau, eps;
+    const double *tau_dev;  // when set, tau is read from device memory at launch
+    double c, alpha, rel_tol, s0;
+    int max_inner, max_bt;
+    int start_at_g;       // iterate starts at g (f is written by the first update)
+    int clamp;            // clamp f >= 0 at the end (Step 3 of Algorithm A1)
+    int mode;             // 0 full solve, 1 energy+grad only, 2 trial only
+    double trial_s;       // mode 2
+    double *out;          // modes 1, 2: results (E, mean d^2)
+    const float *dir;     // mode 2: direction
+    const float *cur;     // modes 1, 2: iterate
+    int level;
+};
+int rof_grid_blocks();
+cudaError_t launch_rof(const RofArgs &a, cudaStream_t s);
+
+} // namespace cbct

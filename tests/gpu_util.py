@@ -1,0 +1,56 @@
+"""Helpers for the GPU parity tests (CUDA library vs FP64 oracle)."""
+import numpy as np
+
+from paper_1001_0599_gb300 import synthetic
+
+# Relative L2 tolerance of one projector call in FP32 against the FP64 oracle,
+# and of a reconstruction after a fixed iteration count.
+TOL_CALL = 1e-5
+TOL_RECON = 1e-4
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+def host(t) -> np.ndarray:
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def f32(x) -> np.ndarray:
+    """Round an FP64 array to the FP32 values both sides consume."""
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+# Geometries spanning several tiles and ragged tails (sizes that are not
+# multiples of the kernels' tiles), nu != nv, single view, one-slice and
+# one-row cases, short scans and anisotropic voxels.
+CASES = {
+    "small": synthetic.workload("small"),
+    "odd": synthetic.Workload("odd", 13, 11, 9, 1.7, 1.3, 2.1, 37, 23, 1.1, 0.9, 7, sad=300.0, sdd=480.0,
+                              arc_deg=200.0),
+    "one_view": synthetic.Workload("one_view", 20, 18, 70, 1.0, 1.0, 0.5, 40, 96, 0.7, 0.4, 1,
+                                   sad=200.0, sdd=350.0),
+    "one_slice": synthetic.Workload("one_slice", 33, 29, 1, 1.0, 1.0, 1.0, 50, 3, 1.0, 1.0, 5,
+                                    sad=150.0, sdd=220.0),
+    "one_row": synthetic.Workload("one_row", 24, 24, 10, 1.0, 1.0, 1.0, 45, 1, 0.9, 0.9, 6,
+                                  sad=150.0, sdd=230.0),
+    "tall": synthetic.Workload("tall", 16, 16, 130, 2.0, 2.0, 0.8, 30, 140, 1.5, 1.2, 4, sad=400.0,
+                               sdd=600.0),
+}
+
+
+def geometries(name):
+    from oracle import oracle as orc
+    from paper_1001_0599_gb300 import cbct
+    wl = CASES[name]
+    return wl, cbct.geometry_from_workload(wl), orc.Geometry.from_workload(wl)
