@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="recon", choices=["recon", "one-iteration"],
+                    help="one-iteration: each step is one FBS iteration on the finest grid with a "
+                         "given step (per-kernel timing and profiler captures)")
     return ap.parse_args()
 
 
@@ -204,7 +207,10 @@ def main():
                                            wl.photons, wl.noise_seed + 1000 * rank)
     g = cbct.geometry_from_workload(wl)
     tv = cbct.TvParams.paper(eps_tv=1e-5)
-    params = cbct.make_recon_params(wl.lam, wl.iters, tv, power_iters=20, clamp=True)
+    if args.mode == "one-iteration":
+        params = cbct.make_recon_params(wl.lam, (1,), tv, taus=[1.28e-5], clamp=True)
+    else:
+        params = cbct.make_recon_params(wl.lam, wl.iters, tv, power_iters=20, clamp=True)
     ws = cbct.workspace(cbct.cbct_workspace_size(g, params))
     stats = cbct.stats_buffer()
     d_y = torch.from_numpy(y.astype(np.float32)).cuda()
@@ -285,6 +291,27 @@ def main():
         e2e = {"value": e2e_s / (args.steps * world), "unit": "s",
                "h2d_bytes_per_step": int(h_y.numel() * 4), "d2h_bytes_per_step": int(h_vol.numel() * 4)}
         del ws_h
+
+    if args.mode == "one-iteration":
+        nnz0 = None
+        try:
+            with open(os.path.join(ROOT, "tests", "golden", "nnz.json")) as fh:
+                nnz0 = float(json.load(fh)["paper"]["0"])
+        except (OSError, KeyError, ValueError):
+            pass
+        out = {"mode": "one-iteration", "steps": args.steps, "ms_per_step": total_ms / args.steps,
+               "clocks": clocks, "kernels": {}}
+        for k, (n, ms) in prof.items():
+            if not n:
+                continue
+            ent = {"launches": n, "avg_ms": ms / n}
+            if nnz0 and k in ("forward_residual", "back_project_step"):
+                ent["tflops"] = 2.0 * nnz0 / (ms / n / 1e3) / 1e12
+                ent["samples_per_s"] = nnz0 / 8.0 / (ms / n / 1e3)
+            out["kernels"][k] = ent
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return 0
 
     # roofline of the dominant kernel
     roof = roofline(prof, wl, args.steps, clocks)

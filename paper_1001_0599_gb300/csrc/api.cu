@@ -179,8 +179,8 @@ static cbct_status check_desc(const cbct_geometry_desc *d)
     if (!d) return fail(CBCT_ERR_INVALID_ARG, "desc is NULL");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nu < 1 || d->nv < 1 || d->n_views < 1)
         return fail(CBCT_ERR_INVALID_ARG, "sizes must be >= 1");
-    if ((double)d->nx * d->ny * d->nz > 4.0e9 || (double)d->n_views * d->nu * d->nv > 4.0e9)
-        return fail(CBCT_ERR_INVALID_ARG, "volume or sinogram above 4e9 elements");
+    if ((double)d->nx * d->ny * d->nz >= 2147483648.0 || (double)d->n_views * d->nu * d->nv > 4.0e9)
+        return fail(CBCT_ERR_INVALID_ARG, "volume must stay below 2^31 voxels, sinogram below 4e9 pixels");
     if (d->n_views > 65535) return fail(CBCT_ERR_INVALID_ARG, "n_views above 65535");
     if (!(d->dx > 0 && d->dy > 0 && d->dz > 0 && d->du > 0 && d->dv > 0))
         return fail(CBCT_ERR_INVALID_ARG, "pitches must be > 0");
@@ -461,7 +461,7 @@ extern "C" cbct_status cbct_residual(const cbct_geometry *G, const float *d_vol,
     cudaStream_t s = (cudaStream_t)stream;
     double *partials = at<double>(ws, L.partials);
     CUDA_TRY(launch_forward(G->lev[0].vg, G->det, d_vol, d_y, d_r, nullptr, partials, 1, s));
-    CUDA_TRY(launch_sum_partials(partials, fp_grid_blocks(G->det), 1, 1, d_sumsq, s));
+    CUDA_TRY(launch_sum_partials(partials, fp_partials_count(G->lev[0].vg, G->det), 1, 1, d_sumsq, s));
     return ok();
 }
 
@@ -746,7 +746,7 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
         for (int it = 0; it < p->iters[lev]; it++, k++) {
             // Step 1: r = ds (P f - y), E2; g = f - tau kappa P^T r
             CUDA_TRY(launch_forward(v, G->det, f, d_sino, r, nullptr, partials, 2, s));
-            CUDA_TRY(launch_e2(partials, fp_grid_blocks(G->det), inv_m, st, s));
+            CUDA_TRY(launch_e2(partials, fp_partials_count(v, G->det), inv_m, st, s));
             CUDA_TRY(launch_back(v, G->det, r, f, g, &st->scale, 0.0, 0.0, nullptr, 1, 1, s));
             // Steps 2-3: ROF from g, clamp fused into its last update
             RofArgs a = rof_base(G, gl, ws, L);

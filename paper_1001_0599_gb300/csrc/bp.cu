@@ -7,12 +7,17 @@
 // xy position falls inside the voxel column's 2dx x 2dy tent support, and,
 // for each such sample, from the detector rows iv whose sample height lies
 // within one dz of z_c. The xy weight of a (iu, j) pair is shared by a whole
-// voxel column, so one warp owns one column and its 32 lanes own 32
-// consecutive z voxels: the (iu, j) loop and the xy weights are warp-uniform
-// and each lane only resolves its rows. Per view, the block stages the
-// detector patch its voxel tile can see into shared memory (odd pitch, so the
-// ~2-rows-per-lane access spreads over the banks); the patch holds ds * r,
-// i.e. the per-ray sample length is folded in once per pixel.
+// voxel column, so one warp owns one column and its 32 lanes own consecutive
+// z voxels: the (iu, j) loop and the xy weights are warp-uniform and each
+// lane only resolves its rows.
+//
+// Per view the block stages the detector patch its voxel tile can see into
+// shared memory column-major ([iu][iv], odd column pitch), padded by NR zero
+// rows, and pre-weighted by the ray's sample length ds. A lane's rows for one
+// sample are then NR consecutive words read with immediate offsets; the
+// z tent weight max(0, 1 - sc |r - q|) zeroes the rows outside the tent, and
+// NR (>= the largest number of rows a voxel's tent can span on this grid) is
+// a template parameter, so the row loop is fully unrolled.
 #include "cbct_internal.cuh"
 
 #include <algorithm>
@@ -25,12 +30,16 @@ constexpr int BP_ZC = 2;              // z chunks of 32 per lane
 constexpr int BP_TZ = 32 * BP_ZC;
 constexpr int BP_WARPS = 8;
 constexpr int BP_COLS_PER_WARP = BP_TX * BP_TY / BP_WARPS;
+constexpr int BP_MAX_ROWS = 64;       // runtime row-loop bound (generic variant)
 
 struct Box {
     float xlo, xhi, ylo, yhi;
 };
 
-// detector column range [*iu0, *iu1] that can see the xy box in view (c, s)
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.f, x); }
+
+// detector columns [iu0, iu1] that can see the xy box in view (c, s), and the
+// box's depth range along the central ray
 __device__ __forceinline__ void box_u_range(const DetGeom &d, float c, float s, const Box &bx,
                                             int &iu0, int &iu1, float &xr_lo, float &xr_hi)
 {
@@ -41,9 +50,9 @@ __device__ __forceinline__ void box_u_range(const DetGeom &d, float c, float s, 
     for (int k = 0; k < 4; k++) {
         const float x = (k & 1) ? bx.xhi : bx.xlo;
         const float y = (k & 2) ? bx.yhi : bx.ylo;
-        const float xr = x * c + y * s;          // depth along the central ray
+        const float xr = x * c + y * s;
         const float yr = -x * s + y * c;
-        const float u = -yr * d.sdd / (xr + d.sad);
+        const float u = -yr * d.sdd * fast_rcp(xr + d.sad);
         umin = fminf(umin, u);
         umax = fmaxf(umax, u);
         xr_lo = fminf(xr_lo, xr);
@@ -53,21 +62,21 @@ __device__ __forceinline__ void box_u_range(const DetGeom &d, float c, float s, 
     iu1 = min((int)ceilf(umax * d.inv_du + d.cu) + 1, d.nu - 1);
 }
 
-template <int MODE, bool PRESCALED>
+// NR > 0: rows per (lane, sample) fully unrolled; NR == 0: runtime loop.
+template <int MODE, bool PRESCALED, int NR>
 __global__ void __launch_bounds__(BP_WARPS * 32)
 bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__restrict__ f,
           float *__restrict__ out, const double *__restrict__ d_scale, float scale_val, float kappa,
-          double *__restrict__ partials, int patch_cap)
+          double *__restrict__ partials, int patch_cap, int pad)
 {
     extern __shared__ float patch[];
-    __shared__ int s_box[5];
+    __shared__ int s_box[6];
     __shared__ double red[32];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int a_base = blockIdx.x * BP_TX, b_base = blockIdx.y * BP_TY, c_base = blockIdx.z * BP_TZ;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nu = d.nu, nv = d.nv;
 
-    // tile support box (voxel centres +- one pitch)
     const float x_first = ((float)a_base - g.cx) * g.dx;
     const float y_first = ((float)b_base - g.cy) * g.dy;
     const Box tile_box{x_first - g.dx, x_first + (float)BP_TX * g.dx,
@@ -87,42 +96,47 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
             int iu0, iu1;
             float xr_lo, xr_hi;
             box_u_range(d, cs.x, cs.y, tile_box, iu0, iu1, xr_lo, xr_hi);
-            // rows: v = z sdd / (depth + sad) over the tile's z and depth ranges
             const float m_near = d.sdd / (xr_lo + d.sad), m_far = d.sdd / (xr_hi + d.sad);
             const float v1 = z_lo * m_near, v2 = z_lo * m_far, v3 = z_hi * m_near, v4 = z_hi * m_far;
             const float vmin = fminf(fminf(v1, v2), fminf(v3, v4));
             const float vmax = fmaxf(fmaxf(v1, v2), fmaxf(v3, v4));
             const int iv0 = max((int)floorf(vmin * d.inv_dv + d.cv) - 1, 0);
             const int iv1 = min((int)ceilf(vmax * d.inv_dv + d.cv) + 1, nv - 1);
-            const int w = iu1 - iu0 + 1, h = iv1 - iv0 + 1;
-            const int pitch = w | 1;
+            const int s0 = iv0 - pad, s1 = iv1 + pad;       // staged rows, zero outside the detector
+            const int w = iu1 - iu0 + 1, h = s1 - s0 + 1;
+            const int hp = h | 1;                           // odd column pitch
             s_box[0] = iu0;
             s_box[1] = iu1;
-            s_box[2] = iv0;
-            s_box[3] = iv1;
-            s_box[4] = (w > 0 && h > 0 && h * pitch <= patch_cap) ? pitch : 0;
+            s_box[2] = s0;
+            s_box[3] = s1;
+            s_box[4] = (iu1 >= iu0 && iv1 >= iv0 && w * hp <= patch_cap) ? hp : 0;
+            s_box[5] = (iu1 >= iu0 && iv1 >= iv0) ? 1 : 0;
         }
         __syncthreads();
-        const int iu0 = s_box[0], iu1 = s_box[1], iv0 = s_box[2], iv1 = s_box[3];
-        const int pitch = s_box[4];
-        const bool staged = pitch > 0;
-        if (iu1 < iu0 || iv1 < iv0) {
+        const int iu0 = s_box[0], iu1 = s_box[1], s0 = s_box[2], s1 = s_box[3];
+        const int hp = s_box[4];
+        if (!s_box[5]) {
             __syncthreads();
             continue;
         }
+        const bool staged = hp > 0;
         if (staged) {
-            const int w = iu1 - iu0 + 1, h = iv1 - iv0 + 1;
+            const int w = iu1 - iu0 + 1, h = s1 - s0 + 1;
             const float *src = sino + (size_t)view * nv * nu;
             for (int r = warp; r < h; r += BP_WARPS) {
-                const int iv = iv0 + r;
+                const int iv = s0 + r;
+                const bool in = iv >= 0 && iv < nv;
                 for (int cc = lane; cc < w; cc += 32) {
                     const int iu = iu0 + cc;
-                    float val = __ldg(src + (size_t)iv * nu + iu);
-                    if (!PRESCALED) {
-                        const float vl = (((float)iv - d.cv) * d.dv) * g.cols[(size_t)view * nu + iu].inv_lxy;
-                        val *= g.drho * sqrtf(1.f + vl * vl);
+                    float val = 0.f;
+                    if (in) {
+                        val = __ldg(src + (size_t)iv * nu + iu);
+                        if (!PRESCALED) {
+                            const float vl = (((float)iv - d.cv) * d.dv) * g.cols[(size_t)view * nu + iu].inv_lxy;
+                            val *= g.drho * sqrtf(1.f + vl * vl);
+                        }
                     }
-                    patch[r * pitch + cc] = val;
+                    patch[cc * hp + r] = val;
                 }
             }
         }
@@ -145,7 +159,7 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
                 // samples of this line inside the column's tent support
                 float tlo = -3.0e38f, thi = 3.0e38f;
                 if (fabsf(rc.ex) > 1e-20f) {
-                    const float inv = 1.f / rc.ex;
+                    const float inv = fast_rcp(rc.ex);
                     const float t1 = (xa - g.dx - rc.mx) * inv, t2 = (xa + g.dx - rc.mx) * inv;
                     tlo = fmaxf(tlo, fminf(t1, t2));
                     thi = fminf(thi, fmaxf(t1, t2));
@@ -153,7 +167,7 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
                     continue;
                 }
                 if (fabsf(rc.ey) > 1e-20f) {
-                    const float inv = 1.f / rc.ey;
+                    const float inv = fast_rcp(rc.ey);
                     const float t1 = (yb - g.dy - rc.my) * inv, t2 = (yb + g.dy - rc.my) * inv;
                     tlo = fmaxf(tlo, fminf(t1, t2));
                     thi = fminf(thi, fmaxf(t1, t2));
@@ -161,12 +175,12 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
                     continue;
                 }
                 if (!(tlo < thi)) continue;
-                const float inv_drho = 1.f / g.drho;
-                int jl = (int)ceilf((tlo + rc.delta) * inv_drho) - 1;
-                int jh = (int)floorf((thi + rc.delta) * inv_drho) + 1;
-                jl = max(jl, (int)rc.jlo);
-                jh = min(jh, (int)rc.jhi);
+                const float inv_drho = fast_rcp(g.drho);
+                const int jl = max((int)ceilf((tlo + rc.delta) * inv_drho) - 1, (int)rc.jlo);
+                const int jh = min((int)floorf((thi + rc.delta) * inv_drho) + 1, (int)rc.jhi);
                 const float sc_base = d.dv * rc.inv_lxy * g.inv_dz;
+                const float *pcol = patch + (iu - iu0) * hp - s0;   // pcol[r] = row r of column iu
+                const float *gcol = sino + (size_t)view * nv * nu + iu;
                 for (int j = jl; j <= jh; ++j) {
                     float fx, fy;
                     sample_xy(g, rc, j, fx, fy);
@@ -178,36 +192,42 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
                     const float wxy = wx * wy;
                     if (wxy == 0.f) continue;  // uniform
                     const float rho = sample_rho(g, rc, j);
-                    const float sc = rho * sc_base;    // z (voxel units) per detector row
-                    const float inv_sc = 1.f / sc;
+                    const float sc = rho * sc_base;        // z (voxel units) per detector row
+                    const float m = fast_rcp(sc);          // tent half-width in rows
 #pragma unroll
                     for (int zc = 0; zc < BP_ZC; ++zc) {
                         const int c = c_base + zc * 32 + lane;
-                        const float q = d.cv + ((float)c - g.cz) * inv_sc;  // row whose sample hits z_c
-                        int r_lo = max((int)ceilf(q - inv_sc), 0);
-                        int r_hi = min((int)floorf(q + inv_sc), nv - 1);
+                        const float q = d.cv + ((float)c - g.cz) * m;   // row whose sample hits z_c
                         float s = 0.f;
-                        if (staged) {
-                            r_lo = max(r_lo, iv0);
-                            r_hi = min(r_hi, iv1);
-                            const float *pp = patch + (iu - iu0);
-                            for (int r = r_lo; r <= r_hi; ++r) {
-                                const float w = fmaxf(1.f - sc * fabsf((float)r - q), 0.f);
-                                s += w * pp[(r - iv0) * pitch];
+                        if (NR > 0 && staged) {
+                            int r0 = (int)ceilf(q - m);
+                            r0 = min(max(r0, s0), s1 - NR + 1);
+                            const float dq = (float)r0 - q;
+                            const float *p = pcol + r0;
+#pragma unroll
+                            for (int t = 0; t < (NR > 0 ? NR : 1); ++t) {
+                                const float w = fmaxf(__fmaf_rn(-sc, fabsf(dq + (float)t), 1.f), 0.f);
+                                s = __fmaf_rn(w, p[t], s);
                             }
                         } else {
-                            const float *src = sino + (size_t)view * nv * nu + iu;
+                            const int r_lo = max((int)ceilf(q - m), 0);
+                            const int r_hi = min(min((int)floorf(q + m), nv - 1), r_lo + BP_MAX_ROWS);
                             for (int r = r_lo; r <= r_hi; ++r) {
-                                const float w = fmaxf(1.f - sc * fabsf((float)r - q), 0.f);
-                                float val = __ldg(src + (size_t)r * nu);
-                                if (!PRESCALED) {
-                                    const float vl = (((float)r - d.cv) * d.dv) * rc.inv_lxy;
-                                    val *= g.drho * sqrtf(1.f + vl * vl);
+                                const float w = fmaxf(__fmaf_rn(-sc, fabsf((float)r - q), 1.f), 0.f);
+                                float val;
+                                if (staged && r >= s0 && r <= s1) {
+                                    val = pcol[r];
+                                } else {
+                                    val = __ldg(gcol + (size_t)r * nu);
+                                    if (!PRESCALED) {
+                                        const float vl = (((float)r - d.cv) * d.dv) * rc.inv_lxy;
+                                        val *= g.drho * sqrtf(1.f + vl * vl);
+                                    }
                                 }
-                                s += w * val;
+                                s = __fmaf_rn(w, val, s);
                             }
                         }
-                        acc[ci][zc] += wxy * s;
+                        acc[ci][zc] = __fmaf_rn(wxy, s, acc[ci][zc]);
                     }
                 }
             }
@@ -253,22 +273,82 @@ int bp_grid_blocks(const VolGeom &v)
     return ((v.nx + BP_TX - 1) / BP_TX) * ((v.ny + BP_TY - 1) / BP_TY) * ((v.nz + BP_TZ - 1) / BP_TZ);
 }
 
+static double support_r(const VolGeom &v)
+{
+    return sqrt(pow(0.5 * (v.nx + 1) * v.dx, 2) + pow(0.5 * (v.ny + 1) * v.dy, 2));
+}
+
+// Largest number of detector rows one voxel's z tent can cover on this grid:
+// floor(2 m) + 1 with m = 1/sc at the smallest sc = rho dv / (L_xy dz).
+static int bp_rows_needed(const VolGeom &v, const DetGeom &d)
+{
+    const double R = support_r(v);
+    const double umax = 0.5 * (d.nu - 1) * d.du;
+    const double lxy_max = sqrt((double)d.sdd * d.sdd + umax * umax);
+    const double sc_min = (d.sad - R) * d.dv / (lxy_max * v.dz);
+    return (int)floor(2.0 / sc_min) + 2;
+}
+
+static int bp_nr_variant(const VolGeom &v, const DetGeom &d)
+{
+    const int need = bp_rows_needed(v, d);
+    for (int nr : {6, 12, 24})
+        if (need <= nr) return nr;
+    return 0;
+}
+
 // Upper bound of the staged patch (host side, FP64, mirrors the device box
-// computation with two pixels of slack); tiles that still do not fit fall
-// back to reading the sinogram from global memory.
+// computation with slack); tiles that still do not fit fall back to reading
+// the sinogram from global memory.
 size_t bp_smem_bytes(const VolGeom &v, const DetGeom &d)
 {
-    const double R = sqrt(pow(0.5 * (v.nx + 1) * v.dx, 2) + pow(0.5 * (v.ny + 1) * v.dy, 2));
+    const double R = support_r(v);
     const double m_max = d.sdd / (d.sad - R), m_min = d.sdd / (d.sad + R);
     const double diag = sqrt(pow((BP_TX + 1) * (double)v.dx, 2) + pow((BP_TY + 1) * (double)v.dy, 2));
     const double w = std::min(diag * m_max / d.du + 6.0, (double)d.nu);
     const double zext = (BP_TZ + 1) * (double)v.dz;
     const double zabs = 0.5 * (v.nz + 1) * v.dz;
-    const double h = std::min((zext * m_max + zabs * (m_max - m_min)) / d.dv + 6.0, (double)d.nv);
-    double cap = (double)((int)ceil(w) | 1) * ceil(h);
+    const int nr = bp_nr_variant(v, d);
+    const double h = std::min((zext * m_max + zabs * (m_max - m_min)) / d.dv + 6.0, (double)d.nv) + 2.0 * nr + 1;
+    double cap = ceil(w) * (double)((int)ceil(h) | 1);
     const double cap_max = 48.0 * 1024.0;   // floats: 192 KB
     if (cap > cap_max) cap = cap_max;
     return (size_t)cap * sizeof(float);
+}
+
+template <int MODE, bool P, int NR>
+static cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const VolGeom &v,
+                              const DetGeom &d, const float *sino, const float *f, float *out,
+                              const double *d_scale, double scale_val, double kappa, double *partials, int cap,
+                              int pad)
+{
+    cudaError_t e = cudaFuncSetAttribute(bp_kernel<MODE, P, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    bp_kernel<MODE, P, NR><<<grid, block, smem, s>>>(v, d, sino, f, out, d_scale, (float)scale_val, (float)kappa,
+                                                     partials, cap, pad);
+    return cudaGetLastError();
+}
+
+template <int MODE, bool P>
+static cudaError_t launch_nr(int nr, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const VolGeom &v,
+                             const DetGeom &d, const float *sino, const float *f, float *out,
+                             const double *d_scale, double scale_val, double kappa, double *partials, int cap)
+{
+    switch (nr) {
+    case 6:
+        return launch_one<MODE, P, 6>(grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa,
+                                      partials, cap, 6);
+    case 12:
+        return launch_one<MODE, P, 12>(grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa,
+                                       partials, cap, 12);
+    case 24:
+        return launch_one<MODE, P, 24>(grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa,
+                                       partials, cap, 24);
+    default:
+        return launch_one<MODE, P, 0>(grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa,
+                                      partials, cap, 0);
+    }
 }
 
 cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, const float *f,
@@ -279,30 +359,24 @@ cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, c
     dim3 block(BP_WARPS * 32);
     const size_t smem = bp_smem_bytes(v, d);
     const int cap = (int)(smem / sizeof(float));
+    const int nr = bp_nr_variant(v, d);
     const int kid = mode == 1 ? K_BP_STEP : K_BP;
-    cudaError_t e = cudaSuccess;
-#define CBCT_BP_LAUNCH(M, P)                                                                        \
-    do {                                                                                            \
-        e = cudaFuncSetAttribute(bp_kernel<M, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                                 (int)smem);                                                        \
-        if (e != cudaSuccess) return e;                                                             \
-        launch_begin(kid, s);                                                                       \
-        bp_kernel<M, P><<<grid, block, smem, s>>>(v, d, sino, f, out, d_scale, (float)scale_val,    \
-                                                  (float)kappa, partials, cap);                     \
-        launch_end(kid, s);                                                                         \
-    } while (0)
-    if (mode == 0) {
-        if (prescaled) CBCT_BP_LAUNCH(0, true);
-        else CBCT_BP_LAUNCH(0, false);
-    } else if (mode == 1) {
-        if (prescaled) CBCT_BP_LAUNCH(1, true);
-        else CBCT_BP_LAUNCH(1, false);
-    } else {
-        if (prescaled) CBCT_BP_LAUNCH(2, true);
-        else CBCT_BP_LAUNCH(2, false);
-    }
-#undef CBCT_BP_LAUNCH
-    return cudaGetLastError();
+    cudaError_t e;
+    launch_begin(kid, s);
+    if (mode == 0)
+        e = launch_nr<0, false>(nr, grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa, partials,
+                                cap);
+    else if (mode == 1 && prescaled)
+        e = launch_nr<1, true>(nr, grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa, partials,
+                               cap);
+    else if (mode == 1)
+        e = launch_nr<1, false>(nr, grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa, partials,
+                                cap);
+    else
+        e = launch_nr<2, false>(nr, grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa, partials,
+                                cap);
+    launch_end(kid, s);
+    return e;
 }
 
 } // namespace cbct

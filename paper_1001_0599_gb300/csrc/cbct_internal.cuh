@@ -186,7 +186,8 @@ void launch_end(int kernel, cudaStream_t s);
 // forward projector. mode 0: out = scale * P vol (scale from d_scale if given)
 // mode 1: out = P vol - y (unscaled residual), partials <- sum r^2
 // mode 2: out = ds * (P vol - y) (residual pre-weighted for the transpose), partials <- sum r^2
-int fp_grid_blocks(const DetGeom &d);
+int fp_grid_blocks(const DetGeom &d);                          // largest grid (workspace sizing)
+int fp_partials_count(const VolGeom &v, const DetGeom &d);      // blocks of the launch for this level
 cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
                            float *out, const double *d_scale, double *partials, int mode,
                            cudaStream_t s);

@@ -4,13 +4,15 @@
 // rho_k = k drho from the source; the sample value is the trilinear
 // interpolant of the voxel grid (zero outside) and each sample carries the
 // length ds = drho |n| / |n_xy|. Because the in-plane position of sample k
-// depends only on (view, iu), one warp takes one detector column iu and 32
-// consecutive rows iv: the xy corners and weights of a sample are
-// warp-uniform, and the 32 lanes read neighbouring z values of the same four
-// voxel columns (z-fastest volume), so the gathers coalesce in L1. The tile
-// of 8 columns x 32 rows is transposed through shared memory and written as
-// 32-byte row segments of the u-fastest sinogram. Residual modes fuse
-// T = P f - y (Sec. II.C.2) and the FP64-grade sum of T^2 into the epilogue.
+// depends only on (view, iu), one warp takes one detector column iu and
+// 32*RPL consecutive rows iv. Per sample the four xy corners and weights are
+// warp-uniform; the warp first blends the four voxel columns over the z range
+// its rows touch (one coalesced z segment per lane, h(c) = sum of the four
+// corner values weighted bilinearly), parks that segment in shared memory,
+// and then every row only interpolates h linearly at its own height. The
+// block's tile of 8 columns x 32*RPL rows is transposed through shared memory
+// and written as 32-byte row segments of the u-fastest sinogram. Residual
+// modes fuse T = P f - y (Sec. II.C.2) and the FP64-grade sum of T^2.
 #include "cbct_internal.cuh"
 
 #include <climits>
@@ -18,51 +20,56 @@
 namespace cbct {
 
 constexpr int FP_WARPS = 8;   // detector columns per block
-constexpr int FP_ROWS = 32;   // detector rows per block (one per lane)
+constexpr int FP_HMAX = 64;   // z values of one blended segment
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-template <int MODE>
+template <int MODE, int RPL>
 __global__ void __launch_bounds__(FP_WARPS * 32)
 fp_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__restrict__ y,
           float *__restrict__ out, const double *__restrict__ d_scale, double *__restrict__ partials)
 {
-    __shared__ float tile[FP_ROWS][FP_WARPS + 1];
-    __shared__ float tile_ds[FP_ROWS][FP_WARPS + 1];
+    constexpr int ROWS = 32 * RPL;
+    __shared__ float tile[ROWS][FP_WARPS + 1];
+    __shared__ float tile_ds[MODE == 2 ? ROWS : 1][FP_WARPS + 1];
+    __shared__ float hbuf[FP_WARPS][FP_HMAX + 2];
     __shared__ double red[32];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int view = blockIdx.z;
     const int iu = blockIdx.x * FP_WARPS + warp;
-    const int iv = blockIdx.y * FP_ROWS + lane;
+    const int row0 = blockIdx.y * ROWS;
+    const int nz = g.nz;
 
-    float acc = 0.f, ds = 0.f;
+    float acc[RPL], tz[RPL], ds[RPL];
+#pragma unroll
+    for (int k = 0; k < RPL; k++) acc[k] = 0.f;
+
     if (iu < d.nu) {  // warp-uniform
         const RayCol rc = g.cols[(size_t)view * d.nu + iu];
-        const float v = ((float)iv - d.cv) * d.dv;
-        const float vl = v * rc.inv_lxy;       // v / L_xy
-        const float tz = vl * g.inv_dz;        // z voxel units per unit rho
-        ds = g.drho * sqrtf(1.f + vl * vl);
-
-        // samples whose z lies in (-1, nz) in voxel units; the rest weigh zero
-        int jlo = rc.jlo, jhi = rc.jhi;
-        if (iv >= d.nv) {
-            jlo = INT_MAX;
-            jhi = INT_MIN;
-        } else if (tz != 0.f) {
-            float r1 = (-1.f - g.cz) / tz, r2 = ((float)g.nz - g.cz) / tz;
-            float rlo = fminf(r1, r2), rhi = fmaxf(r1, r2);
-            rlo = fmaxf(rlo, -1.f);
-            rhi = fminf(rhi, 1.0e7f);
-            int klo = (int)floorf(rlo / g.drho) - 1, khi = (int)ceilf(rhi / g.drho) + 1;
-            jlo = max(jlo, klo - rc.kc);
-            jhi = min(jhi, khi - rc.kc);
+        const float kz = d.dv * rc.inv_lxy;        // v / L_xy per detector row
+#pragma unroll
+        for (int k = 0; k < RPL; k++) {
+            const float vrow = ((float)(row0 + lane + 32 * k) - d.cv);
+            const float vl = vrow * kz;
+            tz[k] = vl * g.inv_dz;
+            ds[k] = g.drho * sqrtf(1.f + vl * vl);
         }
-        const int wlo = __reduce_min_sync(0xffffffffu, jlo);
-        const int whi = __reduce_max_sync(0xffffffffu, jhi);
+        const int last = min(row0 + ROWS - 1, d.nv - 1);
+        const float tz_a = (((float)row0 - d.cv) * kz) * g.inv_dz;
+        const float tz_b = (((float)last - d.cv) * kz) * g.inv_dz;
 
-        const int nx = g.nx, ny = g.ny, nz = g.nz;
-        for (int j = wlo; j <= whi; ++j) {
+        // rows leave the volume through its top or bottom once rho is large
+        int jhi = rc.jhi;
+        float rho_max = 3.0e38f;
+        if (tz_b < 0.f) rho_max = fminf(rho_max, (1.f + g.cz) / (-tz_b));
+        if (tz_a > 0.f) rho_max = fminf(rho_max, ((float)nz - g.cz) / tz_a);
+        if (rho_max < 1.0e7f) jhi = min(jhi, (int)ceilf(rho_max / g.drho) + 1 - rc.kc);
+        const int jlo = rc.jlo;
+
+        const int nx = g.nx, ny = g.ny;
+        float *hb = hbuf[warp];
+        for (int j = jlo; j <= jhi; ++j) {
             float fx, fy;
             sample_xy(g, rc, j, fx, fy);
             const float a0f = floorf(fx), b0f = floorf(fy);
@@ -77,47 +84,84 @@ fp_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__re
             const int ia0 = clampi(a0, 0, nx - 1), ia1 = clampi(a0 + 1, 0, nx - 1);
             const int ib0 = clampi(b0, 0, ny - 1), ib1 = clampi(b0 + 1, 0, ny - 1);
             const float w00 = wx0 * wy0, w01 = wx0 * wy1m, w10 = wx1m * wy0, w11 = wx1m * wy1m;
-            const float *p00 = vol + ((size_t)ia0 * ny + ib0) * nz;
-            const float *p01 = vol + ((size_t)ia0 * ny + ib1) * nz;
-            const float *p10 = vol + ((size_t)ia1 * ny + ib0) * nz;
-            const float *p11 = vol + ((size_t)ia1 * ny + ib1) * nz;
+            const int o00 = (ia0 * ny + ib0) * nz, o01 = (ia0 * ny + ib1) * nz;
+            const int o10 = (ia1 * ny + ib0) * nz, o11 = (ia1 * ny + ib1) * nz;
 
             const float rho = sample_rho(g, rc, j);
-            const float zeta = __fmaf_rn(rho, tz, g.cz);
-            const float c0f = floorf(zeta);
-            const int c0 = (int)c0f;
-            const float wz1 = zeta - c0f;
-            float wz0 = 1.f - wz1, wz1m = wz1;
-            if (c0 < 0 || c0 >= nz) wz0 = 0.f;
-            if (c0 + 1 < 0 || c0 + 1 >= nz) wz1m = 0.f;
-            const int ic0 = clampi(c0, 0, nz - 1), ic1 = clampi(c0 + 1, 0, nz - 1);
-
-            const float col0 = w00 * __ldg(p00 + ic0) + w01 * __ldg(p01 + ic0) +
-                               w10 * __ldg(p10 + ic0) + w11 * __ldg(p11 + ic0);
-            const float col1 = w00 * __ldg(p00 + ic1) + w01 * __ldg(p01 + ic1) +
-                               w10 * __ldg(p10 + ic1) + w11 * __ldg(p11 + ic1);
-            acc += wz0 * col0 + wz1m * col1;
+            const float za = __fmaf_rn(rho, tz_a, g.cz), zb = __fmaf_rn(rho, tz_b, g.cz);
+            const int clo = max((int)floorf(za), -1);
+            const int chi = min((int)floorf(zb) + 1, nz);
+            const int span = chi - clo + 1;
+            if (span <= FP_HMAX) {
+                for (int t = lane; t < span; t += 32) {
+                    const int c = clo + t;
+                    float h = 0.f;
+                    if (c >= 0 && c < nz)
+                        h = w00 * __ldg(vol + o00 + c) + w01 * __ldg(vol + o01 + c) +
+                            w10 * __ldg(vol + o10 + c) + w11 * __ldg(vol + o11 + c);
+                    hb[t] = h;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < RPL; k++) {
+                    const float zeta = __fmaf_rn(rho, tz[k], g.cz);
+                    const float c0f = floorf(zeta);
+                    const int idx = (int)c0f - clo;
+                    if (idx >= 0 && idx <= span - 2) {
+                        const float wz1 = zeta - c0f;
+                        const float h0 = hb[idx], h1 = hb[idx + 1];
+                        acc[k] += h0 + wz1 * (h1 - h0);
+                    }
+                }
+                __syncwarp();
+            } else {
+                // steep rows: direct trilinear gathers per lane
+#pragma unroll
+                for (int k = 0; k < RPL; k++) {
+                    const float zeta = __fmaf_rn(rho, tz[k], g.cz);
+                    const float c0f = floorf(zeta);
+                    const int c0 = (int)c0f;
+                    if (c0 < -1 || c0 >= nz) continue;
+                    const float wz1 = zeta - c0f;
+                    const float wz0 = c0 >= 0 ? 1.f - wz1 : 0.f;
+                    const float wz1m = c0 + 1 < nz ? wz1 : 0.f;
+                    const int ic0 = clampi(c0, 0, nz - 1), ic1 = clampi(c0 + 1, 0, nz - 1);
+                    const float h0 = w00 * __ldg(vol + o00 + ic0) + w01 * __ldg(vol + o01 + ic0) +
+                                     w10 * __ldg(vol + o10 + ic0) + w11 * __ldg(vol + o11 + ic0);
+                    const float h1 = w00 * __ldg(vol + o00 + ic1) + w01 * __ldg(vol + o01 + ic1) +
+                                     w10 * __ldg(vol + o10 + ic1) + w11 * __ldg(vol + o11 + ic1);
+                    acc[k] += wz0 * h0 + wz1m * h1;
+                }
+            }
         }
+    } else {
+#pragma unroll
+        for (int k = 0; k < RPL; k++) ds[k] = 0.f;
     }
 
-    tile[lane][warp] = acc * ds;
-    tile_ds[lane][warp] = ds;
+#pragma unroll
+    for (int k = 0; k < RPL; k++) {
+        tile[lane + 32 * k][warp] = acc[k] * ds[k];
+        if (MODE == 2) tile_ds[lane + 32 * k][warp] = ds[k];
+    }
     __syncthreads();
 
-    // transposed write-back: 32 rows x 8 consecutive columns
-    const int row = threadIdx.x >> 3, col = threadIdx.x & 7;
-    const int oiv = blockIdx.y * FP_ROWS + row, oiu = blockIdx.x * FP_WARPS + col;
+    // transposed write-back: ROWS rows x 8 consecutive columns
     float r2 = 0.f;
-    if (oiv < d.nv && oiu < d.nu) {
-        const size_t o = ((size_t)view * d.nv + oiv) * d.nu + oiu;
-        const float p = tile[row][col];
-        if (MODE == 0) {
-            const float scale = d_scale ? (float)(*d_scale) : 1.f;
-            out[o] = p * scale;
-        } else {
-            const float r = p - __ldg(y + o);
-            r2 = r * r;
-            out[o] = (MODE == 1) ? r : r * tile_ds[row][col];
+    const float scale = (MODE == 0 && d_scale) ? (float)(*d_scale) : 1.f;
+    for (int e = threadIdx.x; e < ROWS * FP_WARPS; e += FP_WARPS * 32) {
+        const int row = e >> 3, col = e & 7;
+        const int oiv = row0 + row, oiu = blockIdx.x * FP_WARPS + col;
+        if (oiv < d.nv && oiu < d.nu) {
+            const size_t o = ((size_t)view * d.nv + oiv) * d.nu + oiu;
+            const float p = tile[row][col];
+            if (MODE == 0) {
+                out[o] = p * scale;
+            } else {
+                const float r = p - __ldg(y + o);
+                r2 += r * r;
+                out[o] = (MODE == 1) ? r : r * tile_ds[MODE == 2 ? row : 0][col];
+            }
         }
     }
     if (MODE != 0) {
@@ -129,25 +173,61 @@ fp_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__re
     }
 }
 
+// rows per lane for a level: the largest of 1, 2, 4 whose warp z span stays
+// within one blended segment at the steepest rows
+int fp_rows_per_lane(const VolGeom &v, const DetGeom &d)
+{
+    const double R = sqrt(pow(0.5 * (v.nx + 1) * v.dx, 2) + pow(0.5 * (v.ny + 1) * v.dy, 2));
+    const double sc_max = (d.sad + R) * d.dv / ((double)d.sdd * v.dz);  // z voxels per detector row
+    int rpl = 1;
+    for (int cand : {2, 4})
+        if (32.0 * cand * sc_max + 3.0 <= FP_HMAX) rpl = cand;
+    return rpl;
+}
+
+static dim3 fp_grid(const DetGeom &d, int rpl)
+{
+    return dim3((d.nu + FP_WARPS - 1) / FP_WARPS, (d.nv + 32 * rpl - 1) / (32 * rpl), d.n_views);
+}
+
 int fp_grid_blocks(const DetGeom &d)
 {
-    return ((d.nu + FP_WARPS - 1) / FP_WARPS) * ((d.nv + FP_ROWS - 1) / FP_ROWS) * d.n_views;
+    const dim3 gr = fp_grid(d, 1);  // the largest grid (one row per lane)
+    return (int)(gr.x * gr.y * gr.z);
+}
+
+template <int MODE>
+static void launch_mode(const VolGeom &v, const DetGeom &d, const float *vol, const float *y, float *out,
+                        const double *d_scale, double *partials, int rpl, cudaStream_t s)
+{
+    const dim3 block(FP_WARPS * 32);
+    if (rpl == 4)
+        fp_kernel<MODE, 4><<<fp_grid(d, 4), block, 0, s>>>(v, d, vol, y, out, d_scale, partials);
+    else if (rpl == 2)
+        fp_kernel<MODE, 2><<<fp_grid(d, 2), block, 0, s>>>(v, d, vol, y, out, d_scale, partials);
+    else
+        fp_kernel<MODE, 1><<<fp_grid(d, 1), block, 0, s>>>(v, d, vol, y, out, d_scale, partials);
+}
+
+int fp_partials_count(const VolGeom &v, const DetGeom &d)
+{
+    const dim3 gr = fp_grid(d, fp_rows_per_lane(v, d));
+    return (int)(gr.x * gr.y * gr.z);
 }
 
 cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
                            float *out, const double *d_scale, double *partials, int mode,
                            cudaStream_t s)
 {
-    dim3 grid((d.nu + FP_WARPS - 1) / FP_WARPS, (d.nv + FP_ROWS - 1) / FP_ROWS, d.n_views);
-    dim3 block(FP_WARPS * 32);
+    const int rpl = fp_rows_per_lane(v, d);
     const int kid = mode == 0 ? K_FP : K_FP_RESID;
     launch_begin(kid, s);
     if (mode == 0)
-        fp_kernel<0><<<grid, block, 0, s>>>(v, d, vol, y, out, d_scale, partials);
+        launch_mode<0>(v, d, vol, y, out, d_scale, partials, rpl, s);
     else if (mode == 1)
-        fp_kernel<1><<<grid, block, 0, s>>>(v, d, vol, y, out, d_scale, partials);
+        launch_mode<1>(v, d, vol, y, out, d_scale, partials, rpl, s);
     else
-        fp_kernel<2><<<grid, block, 0, s>>>(v, d, vol, y, out, d_scale, partials);
+        launch_mode<2>(v, d, vol, y, out, d_scale, partials, rpl, s);
     launch_end(kid, s);
     return cudaGetLastError();
 }
