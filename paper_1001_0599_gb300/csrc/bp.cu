@@ -6,10 +6,13 @@
 // (a, b, c) of P come from the samples j of the in-plane ray lines iu whose
 // xy position falls inside the voxel column's 2dx x 2dy tent support, and,
 // for each such sample, from the detector rows iv whose sample height lies
-// within one dz of z_c. The xy weight of a (iu, j) pair is shared by a whole
-// voxel column, so one warp owns one column and its 32 lanes own consecutive
-// z voxels: the (iu, j) loop and the xy weights are warp-uniform and each
-// lane only resolves its rows.
+// within one dz of z_c. The xy weights of a (iu, j) sample are shared by
+// whole voxel columns and every sample touches at most four columns, so one
+// warp owns a 4 x 4 group of columns (its 32 lanes own consecutive z voxels):
+// the warp visits every sample in the group's footprint once, each lane forms
+// the sample's z tent sum for its voxels once, and the sum is added to the
+// (up to four) columns the sample touches, held in registers and selected by
+// a warp-uniform switch on the sample's xy cell.
 //
 // Per view the block stages the detector patch its voxel tile can see into
 // shared memory column-major ([iu][iv], odd column pitch), padded by NR zero
@@ -25,11 +28,12 @@
 
 namespace cbct {
 
-constexpr int BP_TX = 4, BP_TY = 4;   // voxel columns per block
+constexpr int BP_G = 4;               // a warp owns a BP_G x BP_G group of voxel columns
+constexpr int BP_GX = 2, BP_GY = 2;   // groups per block along x, y
+constexpr int BP_TX = BP_G * BP_GX, BP_TY = BP_G * BP_GY;   // voxel columns per block
 constexpr int BP_ZC = 2;              // z chunks of 32 per lane
 constexpr int BP_TZ = 32 * BP_ZC;
-constexpr int BP_WARPS = 8;
-constexpr int BP_COLS_PER_WARP = BP_TX * BP_TY / BP_WARPS;
+constexpr int BP_WARPS = BP_GX * BP_GY;
 constexpr int BP_MAX_ROWS = 64;       // runtime row-loop bound (generic variant)
 
 struct Box {
@@ -62,7 +66,70 @@ __device__ __forceinline__ void box_u_range(const DetGeom &d, float c, float s, 
     iu1 = min((int)ceilf(umax * d.inv_du + d.cu) + 1, d.nu - 1);
 }
 
+// The z tent sum of one sample for one lane's voxel c: sum over the rows r
+// whose sample height is within one dz of z_c of (1 - sc |r - q|) * row value.
+template <int NR, bool PRESCALED>
+__device__ __forceinline__ float tent_rows(const DetGeom &d, const VolGeom &g, const float *pcol,
+                                           const float *gcol, const RayCol &rc, bool staged, int s0,
+                                           int s1, float q, float m, float sc)
+{
+    float s = 0.f;
+    if (NR > 0 && staged) {
+        int r0 = (int)ceilf(q - m);
+        r0 = min(max(r0, s0), s1 - NR + 1);
+        const float dq = (float)r0 - q;
+        const float *p = pcol + r0;
+#pragma unroll
+        for (int t = 0; t < (NR > 0 ? NR : 1); ++t) {
+            const float w = fmaxf(__fmaf_rn(-sc, fabsf(dq + (float)t), 1.f), 0.f);
+            s = __fmaf_rn(w, p[t], s);
+        }
+    } else {
+        const int r_lo = max((int)ceilf(q - m), 0);
+        const int r_hi = min(min((int)floorf(q + m), d.nv - 1), r_lo + BP_MAX_ROWS);
+        for (int r = r_lo; r <= r_hi; ++r) {
+            const float w = fmaxf(__fmaf_rn(-sc, fabsf((float)r - q), 1.f), 0.f);
+            float val;
+            if (staged && r >= s0 && r <= s1) {
+                val = pcol[r];
+            } else {
+                val = __ldg(gcol + (size_t)r * d.nu);
+                if (!PRESCALED) {
+                    const float vl = (((float)r - d.cv) * d.dv) * rc.inv_lxy;
+                    val *= g.drho * sqrtf(1.f + vl * vl);
+                }
+            }
+            s = __fmaf_rn(w, val, s);
+        }
+    }
+    return s;
+}
+
+// Add a sample's z sums into the (up to four) columns of the warp's G x G
+// group that its xy cell (RA, RB) (relative to the group) touches; corners
+// outside the group belong to a neighbouring group's warp.
+template <int IA, int IB>
+__device__ __forceinline__ void add_one(float (&acc)[BP_G][BP_G][BP_ZC], float w, const float (&s)[BP_ZC])
+{
+    if constexpr (IA >= 0 && IA < BP_G && IB >= 0 && IB < BP_G) {
+#pragma unroll
+        for (int zc = 0; zc < BP_ZC; ++zc) acc[IA][IB][zc] = __fmaf_rn(w, s[zc], acc[IA][IB][zc]);
+    }
+}
+
+template <int RA, int RB>
+__device__ __forceinline__ void add_corners(float (&acc)[BP_G][BP_G][BP_ZC], float w00, float w01, float w10,
+                                            float w11, const float (&s)[BP_ZC])
+{
+    add_one<RA, RB>(acc, w00, s);
+    add_one<RA, RB + 1>(acc, w01, s);
+    add_one<RA + 1, RB>(acc, w10, s);
+    add_one<RA + 1, RB + 1>(acc, w11, s);
+}
+
 // NR > 0: rows per (lane, sample) fully unrolled; NR == 0: runtime loop.
+// Block: BP_WARPS warps, each owning a BP_G x BP_G group of voxel columns and
+// the block's 32*BP_ZC z values (one per lane and chunk).
 template <int MODE, bool PRESCALED, int NR>
 __global__ void __launch_bounds__(BP_WARPS * 32)
 bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__restrict__ f,
@@ -76,6 +143,7 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int a_base = blockIdx.x * BP_TX, b_base = blockIdx.y * BP_TY, c_base = blockIdx.z * BP_TZ;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nu = d.nu, nv = d.nv;
+    const int A = a_base + (warp % BP_GX) * BP_G, B = b_base + (warp / BP_GX) * BP_G;
 
     const float x_first = ((float)a_base - g.cx) * g.dx;
     const float y_first = ((float)b_base - g.cy) * g.dy;
@@ -83,12 +151,17 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
                        y_first - g.dy, y_first + (float)BP_TY * g.dy};
     const float z_lo = ((float)c_base - g.cz - 1.f) * g.dz;
     const float z_hi = ((float)(c_base + BP_TZ) - g.cz) * g.dz;
+    const float xA = ((float)A - g.cx) * g.dx, yB = ((float)B - g.cy) * g.dy;
+    const Box gbox{xA - g.dx, xA + (float)BP_G * g.dx, yB - g.dy, yB + (float)BP_G * g.dy};
+    const bool group_live = A < nx && B < ny;
 
-    float acc[BP_COLS_PER_WARP][BP_ZC];
+    float acc[BP_G][BP_G][BP_ZC];
 #pragma unroll
-    for (int i = 0; i < BP_COLS_PER_WARP; i++)
+    for (int i = 0; i < BP_G; i++)
 #pragma unroll
-        for (int k = 0; k < BP_ZC; k++) acc[i][k] = 0.f;
+        for (int k = 0; k < BP_G; k++)
+#pragma unroll
+            for (int z = 0; z < BP_ZC; z++) acc[i][k][z] = 0.f;
 
     for (int view = 0; view < d.n_views; ++view) {
         const float2 cs = d.views[view];
@@ -142,40 +215,34 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
         }
         __syncthreads();
 
-#pragma unroll
-        for (int ci = 0; ci < BP_COLS_PER_WARP; ++ci) {
-            const int tcol = warp + ci * BP_WARPS;
-            const int a = a_base + (tcol % BP_TX), b = b_base + (tcol / BP_TX);
-            if (a >= nx || b >= ny) continue;  // warp-uniform
-            const float xa = ((float)a - g.cx) * g.dx, yb = ((float)b - g.cy) * g.dy;
-            const Box cbox{xa - g.dx, xa + g.dx, yb - g.dy, yb + g.dy};
+        if (group_live) {  // warp-uniform
             int ju0, ju1;
             float dlo, dhi;
-            box_u_range(d, cs.x, cs.y, cbox, ju0, ju1, dlo, dhi);
+            box_u_range(d, cs.x, cs.y, gbox, ju0, ju1, dlo, dhi);
             ju0 = max(ju0, iu0);
             ju1 = min(ju1, iu1);
+            const float inv_drho = fast_rcp(g.drho);
             for (int iu = ju0; iu <= ju1; ++iu) {
                 const RayCol rc = g.cols[(size_t)view * nu + iu];
-                // samples of this line inside the column's tent support
+                // samples of this line inside the group's support box
                 float tlo = -3.0e38f, thi = 3.0e38f;
                 if (fabsf(rc.ex) > 1e-20f) {
                     const float inv = fast_rcp(rc.ex);
-                    const float t1 = (xa - g.dx - rc.mx) * inv, t2 = (xa + g.dx - rc.mx) * inv;
+                    const float t1 = (gbox.xlo - rc.mx) * inv, t2 = (gbox.xhi - rc.mx) * inv;
                     tlo = fmaxf(tlo, fminf(t1, t2));
                     thi = fminf(thi, fmaxf(t1, t2));
-                } else if (fabsf(rc.mx - xa) >= g.dx) {
+                } else if (!(rc.mx > gbox.xlo && rc.mx < gbox.xhi)) {
                     continue;
                 }
                 if (fabsf(rc.ey) > 1e-20f) {
                     const float inv = fast_rcp(rc.ey);
-                    const float t1 = (yb - g.dy - rc.my) * inv, t2 = (yb + g.dy - rc.my) * inv;
+                    const float t1 = (gbox.ylo - rc.my) * inv, t2 = (gbox.yhi - rc.my) * inv;
                     tlo = fmaxf(tlo, fminf(t1, t2));
                     thi = fminf(thi, fmaxf(t1, t2));
-                } else if (fabsf(rc.my - yb) >= g.dy) {
+                } else if (!(rc.my > gbox.ylo && rc.my < gbox.yhi)) {
                     continue;
                 }
                 if (!(tlo < thi)) continue;
-                const float inv_drho = fast_rcp(g.drho);
                 const int jl = max((int)ceilf((tlo + rc.delta) * inv_drho) - 1, (int)rc.jlo);
                 const int jh = min((int)floorf((thi + rc.delta) * inv_drho) + 1, (int)rc.jhi);
                 const float sc_base = d.dv * rc.inv_lxy * g.inv_dz;
@@ -185,49 +252,37 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
                     float fx, fy;
                     sample_xy(g, rc, j, fx, fy);
                     const float a0f = floorf(fx), b0f = floorf(fy);
-                    const int a0 = (int)a0f, b0 = (int)b0f;
+                    const int ra = (int)a0f - A, rb = (int)b0f - B;
+                    if (ra < -1 || ra >= BP_G || rb < -1 || rb >= BP_G) continue;  // uniform
                     const float wx1 = fx - a0f, wy1 = fy - b0f;
-                    const float wx = (a == a0) ? 1.f - wx1 : ((a == a0 + 1) ? wx1 : 0.f);
-                    const float wy = (b == b0) ? 1.f - wy1 : ((b == b0 + 1) ? wy1 : 0.f);
-                    const float wxy = wx * wy;
-                    if (wxy == 0.f) continue;  // uniform
+                    const float wx0 = 1.f - wx1, wy0 = 1.f - wy1;
                     const float rho = sample_rho(g, rc, j);
                     const float sc = rho * sc_base;        // z (voxel units) per detector row
                     const float m = fast_rcp(sc);          // tent half-width in rows
+                    float s[BP_ZC];
 #pragma unroll
                     for (int zc = 0; zc < BP_ZC; ++zc) {
                         const int c = c_base + zc * 32 + lane;
                         const float q = d.cv + ((float)c - g.cz) * m;   // row whose sample hits z_c
-                        float s = 0.f;
-                        if (NR > 0 && staged) {
-                            int r0 = (int)ceilf(q - m);
-                            r0 = min(max(r0, s0), s1 - NR + 1);
-                            const float dq = (float)r0 - q;
-                            const float *p = pcol + r0;
-#pragma unroll
-                            for (int t = 0; t < (NR > 0 ? NR : 1); ++t) {
-                                const float w = fmaxf(__fmaf_rn(-sc, fabsf(dq + (float)t), 1.f), 0.f);
-                                s = __fmaf_rn(w, p[t], s);
-                            }
-                        } else {
-                            const int r_lo = max((int)ceilf(q - m), 0);
-                            const int r_hi = min(min((int)floorf(q + m), nv - 1), r_lo + BP_MAX_ROWS);
-                            for (int r = r_lo; r <= r_hi; ++r) {
-                                const float w = fmaxf(__fmaf_rn(-sc, fabsf((float)r - q), 1.f), 0.f);
-                                float val;
-                                if (staged && r >= s0 && r <= s1) {
-                                    val = pcol[r];
-                                } else {
-                                    val = __ldg(gcol + (size_t)r * nu);
-                                    if (!PRESCALED) {
-                                        const float vl = (((float)r - d.cv) * d.dv) * rc.inv_lxy;
-                                        val *= g.drho * sqrtf(1.f + vl * vl);
-                                    }
-                                }
-                                s = __fmaf_rn(w, val, s);
-                            }
-                        }
-                        acc[ci][zc] = __fmaf_rn(wxy, s, acc[ci][zc]);
+                        s[zc] = tent_rows<NR, PRESCALED>(d, g, pcol, gcol, rc, staged, s0, s1, q, m, sc);
+                    }
+                    const float w00 = wx0 * wy0, w01 = wx0 * wy1, w10 = wx1 * wy0, w11 = wx1 * wy1;
+                    switch ((ra + 1) * (BP_G + 1) + (rb + 1)) {
+#define CBCT_CORNER(RA, RB)                                                                         \
+    case ((RA) + 1) * (BP_G + 1) + ((RB) + 1):                                                      \
+        add_corners<RA, RB>(acc, w00, w01, w10, w11, s);                                            \
+        break;
+#define CBCT_CORNER_ROW(RA)                                                                         \
+    CBCT_CORNER(RA, -1) CBCT_CORNER(RA, 0) CBCT_CORNER(RA, 1) CBCT_CORNER(RA, 2) CBCT_CORNER(RA, 3)
+                        CBCT_CORNER_ROW(-1)
+                        CBCT_CORNER_ROW(0)
+                        CBCT_CORNER_ROW(1)
+                        CBCT_CORNER_ROW(2)
+                        CBCT_CORNER_ROW(3)
+#undef CBCT_CORNER_ROW
+#undef CBCT_CORNER
+                    default:
+                        break;
                     }
                 }
             }
@@ -239,26 +294,27 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
     const float scale = (MODE == 1) ? (d_scale ? (float)(*d_scale) : scale_val) : 0.f;
     float sq = 0.f;
 #pragma unroll
-    for (int ci = 0; ci < BP_COLS_PER_WARP; ++ci) {
-        const int tcol = warp + ci * BP_WARPS;
-        const int a = a_base + (tcol % BP_TX), b = b_base + (tcol / BP_TX);
-        if (a >= nx || b >= ny) continue;
+    for (int ia = 0; ia < BP_G; ++ia)
 #pragma unroll
-        for (int zc = 0; zc < BP_ZC; ++zc) {
-            const int c = c_base + zc * 32 + lane;
-            if (c >= nz) continue;
-            const size_t idx = ((size_t)a * ny + b) * nz + c;
-            if (MODE == 0) {
-                out[idx] = acc[ci][zc];
-            } else if (MODE == 1) {
-                out[idx] = __fmaf_rn(-scale, acc[ci][zc], __ldg(f + idx));
-            } else {
-                const float w = kappa * acc[ci][zc];
-                out[idx] = w;
-                sq += w * w;
+        for (int ib = 0; ib < BP_G; ++ib) {
+            const int a = A + ia, b = B + ib;
+            if (a >= nx || b >= ny) continue;
+#pragma unroll
+            for (int zc = 0; zc < BP_ZC; ++zc) {
+                const int c = c_base + zc * 32 + lane;
+                if (c >= nz) continue;
+                const size_t idx = ((size_t)a * ny + b) * nz + c;
+                if (MODE == 0) {
+                    out[idx] = acc[ia][ib][zc];
+                } else if (MODE == 1) {
+                    out[idx] = __fmaf_rn(-scale, acc[ia][ib][zc], __ldg(f + idx));
+                } else {
+                    const float w = kappa * acc[ia][ib][zc];
+                    out[idx] = w;
+                    sq += w * w;
+                }
             }
         }
-    }
     if (MODE == 2) {
         DF v[1] = {DF{sq, 0.f}};
         double tot[1];

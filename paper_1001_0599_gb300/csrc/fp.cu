@@ -15,6 +15,7 @@
 // modes fuse T = P f - y (Sec. II.C.2) and the FP64-grade sum of T^2.
 #include "cbct_internal.cuh"
 
+#include <algorithm>
 #include <climits>
 
 namespace cbct {
@@ -173,6 +174,159 @@ fp_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__re
     }
 }
 
+// ---------------------------------------------------------------------------
+// Sheet variant: one block per ray line (view, iu) and all its detector rows.
+// The samples j of the line are processed in chunks of FS_J: (1) one lane per
+// sample computes its xy corners and bilinear weights, (2) the block blends
+// the four voxel columns of every sample over the z range the rows can see,
+// giving the in-plane "sheet" H(j, c), and (3) every thread walks its rows
+// through the chunk, interpolating H linearly at the row's height. No work is
+// repeated across warps; H is padded with two zero entries on each side of z
+// so rows outside the volume need no branches.
+// ---------------------------------------------------------------------------
+constexpr int FS_THREADS = 128;
+constexpr int FS_J = 32;
+
+template <int MODE, int RT>
+__global__ void __launch_bounds__(FS_THREADS)
+fp_sheet_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__restrict__ y,
+                float *__restrict__ out, const double *__restrict__ d_scale, double *__restrict__ partials)
+{
+    extern __shared__ float H[];               // [FS_J][nz + 4]
+    __shared__ int s_o[4][FS_J];
+    __shared__ float s_w[4][FS_J];
+    __shared__ float s_rho[FS_J];
+    __shared__ int s_range[2];
+    __shared__ double red[32];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int iu = blockIdx.x, view = blockIdx.y;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nv = d.nv;
+    const int hs = nz + 4;
+    const RayCol rc = g.cols[(size_t)view * d.nu + iu];
+    const float kz = d.dv * rc.inv_lxy;
+
+    float acc[RT], tz[RT], ds[RT];
+#pragma unroll
+    for (int k = 0; k < RT; k++) {
+        const float vl = ((float)(tid + FS_THREADS * k) - d.cv) * kz;
+        tz[k] = vl * g.inv_dz;
+        ds[k] = g.drho * sqrtf(1.f + vl * vl);
+        acc[k] = 0.f;
+    }
+    const float tz_min = ((0.f - d.cv) * kz) * g.inv_dz;
+    const float tz_max = (((float)(nv - 1) - d.cv) * kz) * g.inv_dz;
+    for (int j = tid; j < FS_J; j += FS_THREADS) {
+        float *Hr = H + j * hs;
+        Hr[0] = Hr[1] = Hr[nz + 2] = Hr[nz + 3] = 0.f;
+    }
+    // rows leave the volume through its top or bottom once rho is large
+    int jhi = rc.jhi;
+    {
+        float rho_max = 3.0e38f;
+        if (tz_max < 0.f) rho_max = fminf(rho_max, (1.f + g.cz) / (-tz_max));
+        if (tz_min > 0.f) rho_max = fminf(rho_max, ((float)nz - g.cz) / tz_min);
+        if (rho_max < 1.0e7f) jhi = min(jhi, (int)ceilf(rho_max / g.drho) + 1 - rc.kc);
+    }
+
+    for (int j0 = rc.jlo; j0 <= jhi; j0 += FS_J) {
+        const int nj = min(FS_J, jhi - j0 + 1);
+        if (warp == 0) {
+            if (lane < nj) {
+                float fx, fy;
+                sample_xy(g, rc, j0 + lane, fx, fy);
+                const float a0f = floorf(fx), b0f = floorf(fy);
+                const int a0 = (int)a0f, b0 = (int)b0f;
+                const float wx1 = fx - a0f, wy1 = fy - b0f;
+                float wx0 = 1.f - wx1, wy0 = 1.f - wy1, wx1m = wx1, wy1m = wy1;
+                if (a0 < 0 || a0 >= nx) wx0 = 0.f;
+                if (a0 + 1 < 0 || a0 + 1 >= nx) wx1m = 0.f;
+                if (b0 < 0 || b0 >= ny) wy0 = 0.f;
+                if (b0 + 1 < 0 || b0 + 1 >= ny) wy1m = 0.f;
+                const int ia0 = clampi(a0, 0, nx - 1), ia1 = clampi(a0 + 1, 0, nx - 1);
+                const int ib0 = clampi(b0, 0, ny - 1), ib1 = clampi(b0 + 1, 0, ny - 1);
+                s_o[0][lane] = (ia0 * ny + ib0) * nz;
+                s_o[1][lane] = (ia0 * ny + ib1) * nz;
+                s_o[2][lane] = (ia1 * ny + ib0) * nz;
+                s_o[3][lane] = (ia1 * ny + ib1) * nz;
+                s_w[0][lane] = wx0 * wy0;
+                s_w[1][lane] = wx0 * wy1m;
+                s_w[2][lane] = wx1m * wy0;
+                s_w[3][lane] = wx1m * wy1m;
+                s_rho[lane] = sample_rho(g, rc, j0 + lane);
+            }
+            if (lane == 0) {
+                // z range the rows can reach over this chunk (rho grows with j)
+                const float ra = sample_rho(g, rc, j0), rb = sample_rho(g, rc, j0 + nj - 1);
+                const float zmin = fminf(fminf(__fmaf_rn(ra, tz_min, g.cz), __fmaf_rn(rb, tz_min, g.cz)),
+                                         fminf(__fmaf_rn(ra, tz_max, g.cz), __fmaf_rn(rb, tz_max, g.cz)));
+                const float zmax = fmaxf(fmaxf(__fmaf_rn(ra, tz_min, g.cz), __fmaf_rn(rb, tz_min, g.cz)),
+                                         fmaxf(__fmaf_rn(ra, tz_max, g.cz), __fmaf_rn(rb, tz_max, g.cz)));
+                s_range[0] = max((int)floorf(zmin) - 1, 0);
+                s_range[1] = min((int)floorf(zmax) + 2, nz - 1);
+            }
+        }
+        __syncthreads();
+        const int clo = s_range[0], chi = s_range[1];
+        for (int jj = warp; jj < nj; jj += FS_THREADS / 32) {
+            const int o0 = s_o[0][jj], o1 = s_o[1][jj], o2 = s_o[2][jj], o3 = s_o[3][jj];
+            const float w0 = s_w[0][jj], w1 = s_w[1][jj], w2 = s_w[2][jj], w3 = s_w[3][jj];
+            float *Hr = H + jj * hs + 2;
+            for (int c = clo + lane; c <= chi; c += 32)
+                Hr[c] = w0 * __ldg(vol + o0 + c) + w1 * __ldg(vol + o1 + c) + w2 * __ldg(vol + o2 + c) +
+                        w3 * __ldg(vol + o3 + c);
+        }
+        __syncthreads();
+        for (int jj = 0; jj < nj; ++jj) {
+            const float rho = s_rho[jj];
+            const float *Hr = H + jj * hs + 2;
+#pragma unroll
+            for (int k = 0; k < RT; k++) {
+                const float zeta = __fmaf_rn(rho, tz[k], g.cz);
+                const float c0f = floorf(zeta);
+                const int c0 = clampi((int)c0f, -2, nz);
+                const float wz1 = zeta - c0f;
+                const float h0 = Hr[c0], h1 = Hr[c0 + 1];
+                acc[k] += h0 + wz1 * (h1 - h0);
+            }
+        }
+        __syncthreads();
+    }
+
+    float r2 = 0.f;
+    const float scale = (MODE == 0 && d_scale) ? (float)(*d_scale) : 1.f;
+#pragma unroll
+    for (int k = 0; k < RT; k++) {
+        const int iv = tid + FS_THREADS * k;
+        if (iv < nv) {
+            const size_t o = ((size_t)view * nv + iv) * d.nu + iu;
+            const float p = acc[k] * ds[k];
+            if (MODE == 0) {
+                out[o] = p * scale;
+            } else {
+                const float r = p - __ldg(y + o);
+                r2 += r * r;
+                out[o] = (MODE == 1) ? r : r * ds[k];
+            }
+        }
+    }
+    if (MODE != 0) {
+        DF v[1] = {DF{r2, 0.f}};
+        double tot[1];
+        block_sum_df<1>(v, red, tot);
+        if (tid == 0) partials[(size_t)view * d.nu + iu] = tot[0];
+    }
+}
+
+// rows per thread of the sheet variant (0: use the warp variant)
+static int fp_sheet_rows(const VolGeom &v, const DetGeom &d)
+{
+    if ((size_t)FS_J * (v.nz + 4) * sizeof(float) > 96 * 1024) return 0;
+    for (int rt : {1, 2, 3, 4, 8})
+        if (d.nv <= FS_THREADS * rt) return rt;
+    return 0;
+}
+
 // rows per lane for a level: the largest of 1, 2, 4 whose warp z span stays
 // within one blended segment at the steepest rows
 int fp_rows_per_lane(const VolGeom &v, const DetGeom &d)
@@ -192,8 +346,8 @@ static dim3 fp_grid(const DetGeom &d, int rpl)
 
 int fp_grid_blocks(const DetGeom &d)
 {
-    const dim3 gr = fp_grid(d, 1);  // the largest grid (one row per lane)
-    return (int)(gr.x * gr.y * gr.z);
+    const dim3 gr = fp_grid(d, 1);  // the largest grid of either variant
+    return (int)std::max<size_t>((size_t)gr.x * gr.y * gr.z, (size_t)d.nu * d.n_views);
 }
 
 template <int MODE>
@@ -211,16 +365,55 @@ static void launch_mode(const VolGeom &v, const DetGeom &d, const float *vol, co
 
 int fp_partials_count(const VolGeom &v, const DetGeom &d)
 {
+    if (fp_sheet_rows(v, d) > 0) return d.nu * d.n_views;
     const dim3 gr = fp_grid(d, fp_rows_per_lane(v, d));
     return (int)(gr.x * gr.y * gr.z);
+}
+
+template <int MODE, int RT>
+static cudaError_t launch_sheet_rt(const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
+                                   float *out, const double *d_scale, double *partials, cudaStream_t s)
+{
+    const size_t smem = (size_t)FS_J * (v.nz + 4) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(fp_sheet_kernel<MODE, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    fp_sheet_kernel<MODE, RT><<<dim3(d.nu, d.n_views), FS_THREADS, smem, s>>>(v, d, vol, y, out, d_scale, partials);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_sheet(int rt, const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
+                                float *out, const double *d_scale, double *partials, cudaStream_t s)
+{
+    switch (rt) {
+    case 1: return launch_sheet_rt<MODE, 1>(v, d, vol, y, out, d_scale, partials, s);
+    case 2: return launch_sheet_rt<MODE, 2>(v, d, vol, y, out, d_scale, partials, s);
+    case 3: return launch_sheet_rt<MODE, 3>(v, d, vol, y, out, d_scale, partials, s);
+    case 4: return launch_sheet_rt<MODE, 4>(v, d, vol, y, out, d_scale, partials, s);
+    default: return launch_sheet_rt<MODE, 8>(v, d, vol, y, out, d_scale, partials, s);
+    }
 }
 
 cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
                            float *out, const double *d_scale, double *partials, int mode,
                            cudaStream_t s)
 {
-    const int rpl = fp_rows_per_lane(v, d);
     const int kid = mode == 0 ? K_FP : K_FP_RESID;
+    const int rt = fp_sheet_rows(v, d);
+    if (rt > 0) {
+        launch_begin(kid, s);
+        cudaError_t e;
+        if (mode == 0)
+            e = launch_sheet<0>(rt, v, d, vol, y, out, d_scale, partials, s);
+        else if (mode == 1)
+            e = launch_sheet<1>(rt, v, d, vol, y, out, d_scale, partials, s);
+        else
+            e = launch_sheet<2>(rt, v, d, vol, y, out, d_scale, partials, s);
+        launch_end(kid, s);
+        return e;
+    }
+    const int rpl = fp_rows_per_lane(v, d);
     launch_begin(kid, s);
     if (mode == 0)
         launch_mode<0>(v, d, vol, y, out, d_scale, partials, rpl, s);

@@ -46,6 +46,9 @@ CASES = {
                                   sad=150.0, sdd=230.0),
     "tall": synthetic.Workload("tall", 16, 16, 130, 2.0, 2.0, 0.8, 30, 140, 1.5, 1.2, 4, sad=400.0,
                                sdd=600.0),
+    # more than 1024 detector rows: exercises the warp-per-column projector variant
+    "very_tall": synthetic.Workload("very_tall", 10, 9, 300, 2.0, 2.0, 0.3, 9, 1100, 2.5, 0.35, 2,
+                                    sad=300.0, sdd=450.0),
 }
 
 
