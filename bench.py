@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--level", type=int, default=0,
+                    help="one-iteration mode: multigrid level (0 = finest)")
     ap.add_argument("--mode", default="recon", choices=["recon", "one-iteration"],
                     help="one-iteration: each step is one FBS iteration on the finest grid with a "
                          "given step (per-kernel timing and profiler captures)")
@@ -208,7 +210,8 @@ def main():
     g = cbct.geometry_from_workload(wl)
     tv = cbct.TvParams.paper(eps_tv=1e-5)
     if args.mode == "one-iteration":
-        params = cbct.make_recon_params(wl.lam, (1,), tv, taus=[1.28e-5], clamp=True)
+        iters = (1,) + (0,) * args.level   # coarsest level listed first
+        params = cbct.make_recon_params(wl.lam, iters, tv, taus=[1.28e-5] * (args.level + 1), clamp=True)
     else:
         params = cbct.make_recon_params(wl.lam, wl.iters, tv, power_iters=20, clamp=True)
     ws = cbct.workspace(cbct.cbct_workspace_size(g, params))
@@ -296,10 +299,10 @@ def main():
         nnz0 = None
         try:
             with open(os.path.join(ROOT, "tests", "golden", "nnz.json")) as fh:
-                nnz0 = float(json.load(fh)["paper"]["0"])
+                nnz0 = float(json.load(fh)["paper"][str(args.level)])
         except (OSError, KeyError, ValueError):
             pass
-        out = {"mode": "one-iteration", "steps": args.steps, "ms_per_step": total_ms / args.steps,
+        out = {"mode": "one-iteration", "level": args.level, "steps": args.steps, "ms_per_step": total_ms / args.steps,
                "clocks": clocks, "kernels": {}}
         for k, (n, ms) in prof.items():
             if not n:

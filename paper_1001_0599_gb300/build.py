@@ -17,7 +17,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcbct.so")
-SOURCES = ["api.cu", "fp.cu", "bp.cu", "tv.cu", "misc.cu"]
+# (source, object, extra nvcc flags): the transpose's template variants are
+# split over three objects so they compile in parallel
+SOURCES = [("api.cu", "api.o", ()), ("fp.cu", "fp.o", ()), ("bp.cu", "bp0.o", ("-DBP_MODE_UNIT=0",)),
+           ("bp.cu", "bp1.o", ("-DBP_MODE_UNIT=1",)), ("bp.cu", "bp2.o", ("-DBP_MODE_UNIT=2",)),
+           ("tv.cu", "tv.o", ()), ("misc.cu", "misc.o", ())]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -42,12 +46,13 @@ def _deps():
     return max(os.path.getmtime(h) for h in hdrs)
 
 
-def _compile(src: str, verbose: bool, extra) -> str:
-    obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+def _compile(unit, verbose: bool, extra) -> str:
+    src, objname, defs = unit
+    obj = os.path.join(BUILD, objname)
     path = os.path.join(CSRC, src)
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(path), _deps()):
         return obj
-    cmd = [nvcc(), *_flags(extra), "-c", path, "-o", obj + ".tmp"]
+    cmd = [nvcc(), *_flags(tuple(extra) + tuple(defs)), "-c", path, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)

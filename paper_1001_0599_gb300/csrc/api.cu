@@ -80,6 +80,8 @@ void launch_begin(int kernel, cudaStream_t s)
     cudaEventRecord(p.start, s);
 }
 
+void note_extra_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 void launch_end(int kernel, cudaStream_t s)
 {
     if (!g_prof_on) return;
@@ -358,7 +360,7 @@ static double kappa_of(const VolGeom &v, const DetGeom &d) { return 2.0 * (doubl
 // workspace
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t state, partials, r, g, d, coarse[CBCT_MAX_LEVELS], replay, stats, hsino, hvol, total;
+    size_t state, partials, r, g, d, split, coarse[CBCT_MAX_LEVELS], replay, stats, hsino, hvol, total;
     int n_partials;
 };
 
@@ -372,7 +374,7 @@ static Layout layout(const cbct_geometry *G, const cbct_recon_params *p, bool ho
     L.state = off;
     off = align_up(off + sizeof(DevState));
     int np = fp_grid_blocks(G->det);
-    np = std::max(np, bp_grid_blocks(v0));
+    for (int l = 0; l < G->n_levels; l++) np = std::max(np, bp_grid_blocks(G->lev[l].vg));
     np = std::max(np, 4 * rof_grid_blocks());
     L.n_partials = np;
     L.partials = off;
@@ -383,6 +385,10 @@ static Layout layout(const cbct_geometry *G, const cbct_recon_params *p, bool ho
     off = align_up(off + sizeof(float) * nvox(v0));
     L.d = off;
     off = align_up(off + sizeof(float) * nvox(v0));
+    size_t split = 0;
+    for (int l = 0; l < G->n_levels; l++) split = std::max(split, bp_split_floats(G->lev[l].vg, G->det));
+    L.split = off;
+    off = align_up(off + sizeof(float) * split);
     const int levels = p ? std::max(1, std::min(p->n_levels, CBCT_MAX_LEVELS)) : 1;
     for (int l = 1; l < levels && l < G->n_levels; l++) {
         L.coarse[l] = off;
@@ -470,7 +476,7 @@ extern "C" cbct_status cbct_back_project(const cbct_geometry *G, const float *d_
     CHECK(check_geom(G));
     CHECK(check_ptr(d_sino, "d_sino"));
     CHECK(check_ptr(d_vol, "d_vol"));
-    CUDA_TRY(launch_back(G->lev[0].vg, G->det, d_sino, nullptr, d_vol, nullptr, 0.0, 0.0, nullptr, 0, 0,
+    CUDA_TRY(launch_back(G->lev[0].vg, G->det, d_sino, nullptr, d_vol, nullptr, 0.0, 0.0, nullptr, 0, 0, nullptr,
                          (cudaStream_t)stream));
     return ok();
 }
@@ -484,7 +490,7 @@ extern "C" cbct_status cbct_gradient_step(const cbct_geometry *G, const float *d
     CHECK(check_ptr(d_g, "d_g"));
     if (d_g == d_f) return fail(CBCT_ERR_INVALID_ARG, "d_g must not alias d_f");
     if (!std::isfinite(scale)) return fail(CBCT_ERR_INVALID_ARG, "scale not finite");
-    CUDA_TRY(launch_back(G->lev[0].vg, G->det, d_r, d_f, d_g, nullptr, scale, 0.0, nullptr, 1, 0,
+    CUDA_TRY(launch_back(G->lev[0].vg, G->det, d_r, d_f, d_g, nullptr, scale, 0.0, nullptr, 1, 0, nullptr,
                          (cudaStream_t)stream));
     return ok();
 }
@@ -646,9 +652,10 @@ static cbct_status run_power(const cbct_geometry *G, int level, int n_iter, void
     CUDA_TRY(launch_fill(w, nvox(v), 1.f, s));
     for (int it = 0; it < n_iter; it++) {
         CUDA_TRY(launch_forward(v, G->det, w, nullptr, sino, &st->inv_wnorm, nullptr, 0, s));
-        CUDA_TRY(launch_back(v, G->det, sino, nullptr, w, nullptr, 0.0, kappa, partials, 2, 0, s));
-        CUDA_TRY(launch_power_update(st, partials, bp_grid_blocks(v), kappa, it == 0, it == n_iter - 1,
-                                     d_L_out, s));
+        CUDA_TRY(launch_back(v, G->det, sino, nullptr, w, nullptr, 0.0, kappa, partials, 2, 0,
+                             at<float>(ws, L.split), s));
+        CUDA_TRY(launch_power_update(st, partials, bp_partials_count(v, G->det, true), kappa, it == 0,
+                                     it == n_iter - 1, d_L_out, s));
     }
     return CBCT_OK;
 }
@@ -747,7 +754,7 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
             // Step 1: r = ds (P f - y), E2; g = f - tau kappa P^T r
             CUDA_TRY(launch_forward(v, G->det, f, d_sino, r, nullptr, partials, 2, s));
             CUDA_TRY(launch_e2(partials, fp_partials_count(v, G->det), inv_m, st, s));
-            CUDA_TRY(launch_back(v, G->det, r, f, g, &st->scale, 0.0, 0.0, nullptr, 1, 1, s));
+            CUDA_TRY(launch_back(v, G->det, r, f, g, &st->scale, 0.0, 0.0, nullptr, 1, 1, at<float>(ws, L.split), s));
             // Steps 2-3: ROF from g, clamp fused into its last update
             RofArgs a = rof_base(G, gl, ws, L);
             a.g = g;

@@ -23,6 +23,10 @@
 // a template parameter, so the row loop is fully unrolled.
 #include "cbct_internal.cuh"
 
+#ifndef BP_MODE_UNIT
+#define BP_MODE_UNIT 0
+#endif
+
 #include <algorithm>
 #include <cmath>
 
@@ -31,14 +35,37 @@ namespace cbct {
 constexpr int BP_G = 4;               // a warp owns a BP_G x BP_G group of voxel columns
 constexpr int BP_GX = 2, BP_GY = 2;   // groups per block along x, y
 constexpr int BP_TX = BP_G * BP_GX, BP_TY = BP_G * BP_GY;   // voxel columns per block
-constexpr int BP_ZC = 2;              // z chunks of 32 per lane
-constexpr int BP_TZ = 32 * BP_ZC;
 constexpr int BP_WARPS = BP_GX * BP_GY;
 constexpr int BP_MAX_ROWS = 64;       // runtime row-loop bound (generic variant)
 
 struct Box {
     float xlo, xhi, ylo, yhi;
 };
+
+// One sample of a warp's footprint list: xy cell relative to the group in the
+// low 8 bits and the detector column above them (-1: outside the group),
+// patch column offset, bilinear corner weights, z voxels per detector row
+// (sc) and its reciprocal.
+struct __align__(16) SampleEntry {
+    int cell, col;
+    float w00, w01, w10, w11, sc, m;
+};
+constexpr int BP_ENTRIES = 96;    // entries per warp and batch
+
+struct BpLaunch {
+    VolGeom v;
+    DetGeom d;
+    const float *sino;
+    const float *f;
+    float *out;
+    const double *d_scale;
+    float scale_val, kappa;
+    double *partials;
+    int cap, zblocks, vpg;
+};
+
+template <int MODE, bool P>
+cudaError_t bp_dispatch(int zc, int nr, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const BpLaunch &L);
 
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.f, x); }
 
@@ -79,11 +106,16 @@ __device__ __forceinline__ float tent_rows(const DetGeom &d, const VolGeom &g, c
         r0 = min(max(r0, s0), s1 - NR + 1);
         const float dq = (float)r0 - q;
         const float *p = pcol + r0;
+        float s2 = 0.f;
 #pragma unroll
         for (int t = 0; t < (NR > 0 ? NR : 1); ++t) {
             const float w = fmaxf(__fmaf_rn(-sc, fabsf(dq + (float)t), 1.f), 0.f);
-            s = __fmaf_rn(w, p[t], s);
+            if (t & 1)
+                s2 = __fmaf_rn(w, p[t], s2);
+            else
+                s = __fmaf_rn(w, p[t], s);
         }
+        s += s2;
     } else {
         const int r_lo = max((int)ceilf(q - m), 0);
         const int r_hi = min(min((int)floorf(q + m), d.nv - 1), r_lo + BP_MAX_ROWS);
@@ -105,44 +137,75 @@ __device__ __forceinline__ float tent_rows(const DetGeom &d, const VolGeom &g, c
     return s;
 }
 
+// Staged variant only (no global fallback): NR rows from the padded patch.
+template <int NR>
+__device__ __forceinline__ float tent_rows_staged(const float *pcol, bool staged, int s0, int s1, float q, float m,
+                                                  float sc)
+{
+    float s = 0.f, s2 = 0.f;
+    if (NR > 0 && staged) {
+        int r0 = (int)ceilf(q - m);
+        r0 = min(max(r0, s0), s1 - NR + 1);
+        const float dq = (float)r0 - q;
+        const float *p = pcol + r0;
+#pragma unroll
+        for (int t = 0; t < (NR > 0 ? NR : 1); ++t) {
+            const float w = fmaxf(__fmaf_rn(-sc, fabsf(dq + (float)t), 1.f), 0.f);
+            if (t & 1)
+                s2 = __fmaf_rn(w, p[t], s2);
+            else
+                s = __fmaf_rn(w, p[t], s);
+        }
+    }
+    return s + s2;
+}
+
 // Add a sample's z sums into the (up to four) columns of the warp's G x G
 // group that its xy cell (RA, RB) (relative to the group) touches; corners
 // outside the group belong to a neighbouring group's warp.
-template <int IA, int IB>
-__device__ __forceinline__ void add_one(float (&acc)[BP_G][BP_G][BP_ZC], float w, const float (&s)[BP_ZC])
+template <int IA, int IB, int ZC>
+__device__ __forceinline__ void add_one(float (&acc)[BP_G][BP_G][ZC], float w, const float (&s)[ZC])
 {
     if constexpr (IA >= 0 && IA < BP_G && IB >= 0 && IB < BP_G) {
 #pragma unroll
-        for (int zc = 0; zc < BP_ZC; ++zc) acc[IA][IB][zc] = __fmaf_rn(w, s[zc], acc[IA][IB][zc]);
+        for (int zc = 0; zc < ZC; ++zc) acc[IA][IB][zc] = __fmaf_rn(w, s[zc], acc[IA][IB][zc]);
     }
 }
 
-template <int RA, int RB>
-__device__ __forceinline__ void add_corners(float (&acc)[BP_G][BP_G][BP_ZC], float w00, float w01, float w10,
-                                            float w11, const float (&s)[BP_ZC])
+template <int RA, int RB, int ZC>
+__device__ __forceinline__ void add_corners(float (&acc)[BP_G][BP_G][ZC], float w00, float w01, float w10,
+                                            float w11, const float (&s)[ZC])
 {
-    add_one<RA, RB>(acc, w00, s);
-    add_one<RA, RB + 1>(acc, w01, s);
-    add_one<RA + 1, RB>(acc, w10, s);
-    add_one<RA + 1, RB + 1>(acc, w11, s);
+    add_one<RA, RB, ZC>(acc, w00, s);
+    add_one<RA, RB + 1, ZC>(acc, w01, s);
+    add_one<RA + 1, RB, ZC>(acc, w10, s);
+    add_one<RA + 1, RB + 1, ZC>(acc, w11, s);
 }
 
 // NR > 0: rows per (lane, sample) fully unrolled; NR == 0: runtime loop.
 // Block: BP_WARPS warps, each owning a BP_G x BP_G group of voxel columns and
-// the block's 32*BP_ZC z values (one per lane and chunk).
-template <int MODE, bool PRESCALED, int NR>
+// the block's 32*ZC z values (one per lane and chunk). With a view split
+// (MODE 3) block z index = z block + zblocks * view group, and the block adds
+// only its group's views and writes the raw sums to out + group * N_vox.
+template <int MODE, bool PRESCALED, int NR, int ZC>
 __global__ void __launch_bounds__(BP_WARPS * 32)
 bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__restrict__ f,
           float *__restrict__ out, const double *__restrict__ d_scale, float scale_val, float kappa,
-          double *__restrict__ partials, int patch_cap, int pad)
+          double *__restrict__ partials, int patch_cap, int pad, int zblocks, int views_per_group)
 {
+    constexpr int BP_ZC = ZC;
+    constexpr int BP_TZ = 32 * ZC;
     extern __shared__ float patch[];
     __shared__ int s_box[6];
     __shared__ double red[32];
+    __shared__ SampleEntry s_ent[BP_WARPS * BP_ENTRIES];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int a_base = blockIdx.x * BP_TX, b_base = blockIdx.y * BP_TY, c_base = blockIdx.z * BP_TZ;
+    const int zb = (int)blockIdx.z % zblocks, vg = (int)blockIdx.z / zblocks;
+    const int a_base = blockIdx.x * BP_TX, b_base = blockIdx.y * BP_TY, c_base = zb * BP_TZ;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nu = d.nu, nv = d.nv;
+    const int view_begin = vg * views_per_group;
+    const int view_end = min(d.n_views, view_begin + views_per_group);
     const int A = a_base + (warp % BP_GX) * BP_G, B = b_base + (warp / BP_GX) * BP_G;
 
     const float x_first = ((float)a_base - g.cx) * g.dx;
@@ -163,7 +226,7 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
 #pragma unroll
             for (int z = 0; z < BP_ZC; z++) acc[i][k][z] = 0.f;
 
-    for (int view = 0; view < d.n_views; ++view) {
+    for (int view = view_begin; view < view_end; ++view) {
         const float2 cs = d.views[view];
         if (threadIdx.x == 0) {
             int iu0, iu1;
@@ -221,69 +284,120 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
             box_u_range(d, cs.x, cs.y, gbox, ju0, ju1, dlo, dhi);
             ju0 = max(ju0, iu0);
             ju1 = min(ju1, iu1);
+            SampleEntry *ent = s_ent + warp * BP_ENTRIES;
             const float inv_drho = fast_rcp(g.drho);
-            for (int iu = ju0; iu <= ju1; ++iu) {
-                const RayCol rc = g.cols[(size_t)view * nu + iu];
-                // samples of this line inside the group's support box
-                float tlo = -3.0e38f, thi = 3.0e38f;
-                if (fabsf(rc.ex) > 1e-20f) {
-                    const float inv = fast_rcp(rc.ex);
-                    const float t1 = (gbox.xlo - rc.mx) * inv, t2 = (gbox.xhi - rc.mx) * inv;
-                    tlo = fmaxf(tlo, fminf(t1, t2));
-                    thi = fminf(thi, fmaxf(t1, t2));
-                } else if (!(rc.mx > gbox.xlo && rc.mx < gbox.xhi)) {
-                    continue;
-                }
-                if (fabsf(rc.ey) > 1e-20f) {
-                    const float inv = fast_rcp(rc.ey);
-                    const float t1 = (gbox.ylo - rc.my) * inv, t2 = (gbox.yhi - rc.my) * inv;
-                    tlo = fmaxf(tlo, fminf(t1, t2));
-                    thi = fminf(thi, fmaxf(t1, t2));
-                } else if (!(rc.my > gbox.ylo && rc.my < gbox.yhi)) {
-                    continue;
-                }
-                if (!(tlo < thi)) continue;
-                const int jl = max((int)ceilf((tlo + rc.delta) * inv_drho) - 1, (int)rc.jlo);
-                const int jh = min((int)floorf((thi + rc.delta) * inv_drho) + 1, (int)rc.jhi);
-                const float sc_base = d.dv * rc.inv_lxy * g.inv_dz;
-                const float *pcol = patch + (iu - iu0) * hp - s0;   // pcol[r] = row r of column iu
-                const float *gcol = sino + (size_t)view * nv * nu + iu;
-                for (int j = jl; j <= jh; ++j) {
-                    float fx, fy;
-                    sample_xy(g, rc, j, fx, fy);
-                    const float a0f = floorf(fx), b0f = floorf(fy);
-                    const int ra = (int)a0f - A, rb = (int)b0f - B;
-                    if (ra < -1 || ra >= BP_G || rb < -1 || rb >= BP_G) continue;  // uniform
-                    const float wx1 = fx - a0f, wy1 = fy - b0f;
-                    const float wx0 = 1.f - wx1, wy0 = 1.f - wy1;
-                    const float rho = sample_rho(g, rc, j);
-                    const float sc = rho * sc_base;        // z (voxel units) per detector row
-                    const float m = fast_rcp(sc);          // tent half-width in rows
-                    float s[BP_ZC];
-#pragma unroll
-                    for (int zc = 0; zc < BP_ZC; ++zc) {
-                        const int c = c_base + zc * 32 + lane;
-                        const float q = d.cv + ((float)c - g.cz) * m;   // row whose sample hits z_c
-                        s[zc] = tent_rows<NR, PRESCALED>(d, g, pcol, gcol, rc, staged, s0, s1, q, m, sc);
+            // lanes take detector columns; each enumerates its line's samples in
+            // the group's footprint (entries ordered by column, then sample)
+            for (int iub = ju0; iub <= ju1; iub += 32) {
+                const int iu = iub + lane;
+                int jl = 0, jh = -1;
+                RayCol rc{};
+                if (iu <= ju1) {
+                    rc = g.cols[(size_t)view * nu + iu];
+                    float tlo = -3.0e38f, thi = 3.0e38f;
+                    bool hit = true;
+                    if (fabsf(rc.ex) > 1e-20f) {
+                        const float inv = fast_rcp(rc.ex);
+                        const float t1 = (gbox.xlo - rc.mx) * inv, t2 = (gbox.xhi - rc.mx) * inv;
+                        tlo = fmaxf(tlo, fminf(t1, t2));
+                        thi = fminf(thi, fmaxf(t1, t2));
+                    } else if (!(rc.mx > gbox.xlo && rc.mx < gbox.xhi)) {
+                        hit = false;
                     }
-                    const float w00 = wx0 * wy0, w01 = wx0 * wy1, w10 = wx1 * wy0, w11 = wx1 * wy1;
-                    switch ((ra + 1) * (BP_G + 1) + (rb + 1)) {
+                    if (fabsf(rc.ey) > 1e-20f) {
+                        const float inv = fast_rcp(rc.ey);
+                        const float t1 = (gbox.ylo - rc.my) * inv, t2 = (gbox.yhi - rc.my) * inv;
+                        tlo = fmaxf(tlo, fminf(t1, t2));
+                        thi = fminf(thi, fmaxf(t1, t2));
+                    } else if (!(rc.my > gbox.ylo && rc.my < gbox.yhi)) {
+                        hit = false;
+                    }
+                    if (hit && tlo < thi) {
+                        jl = max((int)ceilf((tlo + rc.delta) * inv_drho) - 1, (int)rc.jlo);
+                        jh = min((int)floorf((thi + rc.delta) * inv_drho) + 1, (int)rc.jhi);
+                    }
+                }
+                const int cnt = max(jh - jl + 1, 0);
+                int incl = cnt;  // inclusive warp scan of the counts
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v2 = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v2;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                const int first = incl - cnt;
+                const float sc_base = d.dv * rc.inv_lxy * g.inv_dz;
+                const int col_off = (iu - iu0) * hp - s0;
+                for (int b0 = 0; b0 < total; b0 += BP_ENTRIES) {
+                    // fill this batch's entries
+                    const int lo = max(first, b0), hi = min(first + cnt, b0 + BP_ENTRIES);
+                    for (int e = lo; e < hi; ++e) {
+                        const int j = jl + (e - first);
+                        float fx, fy;
+                        sample_xy(g, rc, j, fx, fy);
+                        const float a0f = floorf(fx), b0f = floorf(fy);
+                        const int ra = (int)a0f - A, rb = (int)b0f - B;
+                        const float wx1 = fx - a0f, wy1 = fy - b0f;
+                        const float wx0 = 1.f - wx1, wy0 = 1.f - wy1;
+                        const float sc = sample_rho(g, rc, j) * sc_base;
+                        SampleEntry en;
+                        en.cell = (ra < -1 || ra >= BP_G || rb < -1 || rb >= BP_G)
+                                      ? -1
+                                      : ((ra + 1) * (BP_G + 1) + (rb + 1)) | (iu << 8);
+                        en.col = col_off;
+                        en.w00 = wx0 * wy0;
+                        en.w01 = wx0 * wy1;
+                        en.w10 = wx1 * wy0;
+                        en.w11 = wx1 * wy1;
+                        en.sc = sc;
+                        en.m = fast_rcp(sc);
+                        ent[e - b0] = en;
+                    }
+                    __syncwarp();
+                    const int nb = min(BP_ENTRIES, total - b0);
+                    for (int e = 0; e < nb; ++e) {
+                        const SampleEntry en = ent[e];
+                        if (en.cell < 0) continue;  // uniform
+                        const float *pcol = patch + en.col;
+                        float sv[BP_ZC];
+#pragma unroll
+                        for (int zc = 0; zc < BP_ZC; ++zc) {
+                            const int c = c_base + zc * 32 + lane;
+                            const float q = d.cv + ((float)c - g.cz) * en.m;   // row whose sample hits z_c
+                            sv[zc] = tent_rows_staged<NR>(pcol, staged, s0, s1, q, en.m, en.sc);
+                        }
+                        if (!(NR > 0 && staged)) {
+                            // generic path: rows outside the staged patch come from global memory
+                            const int iu_e = en.cell >> 8;
+                            const RayCol rce = g.cols[(size_t)view * nu + iu_e];
+                            const float *gcol = sino + (size_t)view * nv * nu + iu_e;
+#pragma unroll
+                            for (int zc = 0; zc < BP_ZC; ++zc) {
+                                const int c = c_base + zc * 32 + lane;
+                                const float q = d.cv + ((float)c - g.cz) * en.m;
+                                sv[zc] = tent_rows<0, PRESCALED>(d, g, pcol, gcol, rce, staged, s0, s1, q, en.m,
+                                                                 en.sc);
+                            }
+                        }
+                        switch (en.cell & 255) {
 #define CBCT_CORNER(RA, RB)                                                                         \
     case ((RA) + 1) * (BP_G + 1) + ((RB) + 1):                                                      \
-        add_corners<RA, RB>(acc, w00, w01, w10, w11, s);                                            \
+        add_corners<RA, RB, ZC>(acc, en.w00, en.w01, en.w10, en.w11, sv);                           \
         break;
 #define CBCT_CORNER_ROW(RA)                                                                         \
     CBCT_CORNER(RA, -1) CBCT_CORNER(RA, 0) CBCT_CORNER(RA, 1) CBCT_CORNER(RA, 2) CBCT_CORNER(RA, 3)
-                        CBCT_CORNER_ROW(-1)
-                        CBCT_CORNER_ROW(0)
-                        CBCT_CORNER_ROW(1)
-                        CBCT_CORNER_ROW(2)
-                        CBCT_CORNER_ROW(3)
+                            CBCT_CORNER_ROW(-1)
+                            CBCT_CORNER_ROW(0)
+                            CBCT_CORNER_ROW(1)
+                            CBCT_CORNER_ROW(2)
+                            CBCT_CORNER_ROW(3)
 #undef CBCT_CORNER_ROW
 #undef CBCT_CORNER
-                    default:
-                        break;
+                        default:
+                            break;
+                        }
                     }
+                    __syncwarp();
                 }
             }
         }
@@ -306,6 +420,8 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
                 const size_t idx = ((size_t)a * ny + b) * nz + c;
                 if (MODE == 0) {
                     out[idx] = acc[ia][ib][zc];
+                } else if (MODE == 3) {
+                    out[(size_t)vg * ((size_t)nx * ny * nz) + idx] = acc[ia][ib][zc];
                 } else if (MODE == 1) {
                     out[idx] = __fmaf_rn(-scale, acc[ia][ib][zc], __ldg(f + idx));
                 } else {
@@ -324,9 +440,50 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
     }
 }
 
+#if BP_MODE_UNIT == 0
+static int bp_zc(const VolGeom &v) { return v.nz <= 32 ? 1 : 2; }
+
+static int bp_zblocks(const VolGeom &v) { return (v.nz + 32 * bp_zc(v) - 1) / (32 * bp_zc(v)); }
+
+static int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n < 1) n = 1;
+    }
+    return n;
+}
+
+// View groups: coarse grids have too few voxel tiles to fill the GPU, so the
+// views are split over several blocks whose raw sums a combine pass adds in
+// a fixed order.
+int bp_view_groups(const VolGeom &v, const DetGeom &d)
+{
+    const long base = (long)((v.nx + BP_TX - 1) / BP_TX) * ((v.ny + BP_TY - 1) / BP_TY) * bp_zblocks(v);
+    const long target = 4L * sm_count();
+    if (base >= target) return 1;
+    long groups = (target + base - 1) / base;
+    if (groups > d.n_views) groups = d.n_views;
+    const int per = (int)((d.n_views + groups - 1) / groups);
+    return (d.n_views + per - 1) / per;
+}
+
+size_t bp_split_floats(const VolGeom &v, const DetGeom &d)
+{
+    const int gcount = bp_view_groups(v, d);
+    return gcount > 1 ? (size_t)gcount * v.nx * v.ny * v.nz : 0;
+}
+
+constexpr int BPC_THREADS = 256;
+constexpr int BPC_BLOCKS = 1024;
+
 int bp_grid_blocks(const VolGeom &v)
 {
-    return ((v.nx + BP_TX - 1) / BP_TX) * ((v.ny + BP_TY - 1) / BP_TY) * ((v.nz + BP_TZ - 1) / BP_TZ);
+    const int direct = ((v.nx + BP_TX - 1) / BP_TX) * ((v.ny + BP_TY - 1) / BP_TY) * bp_zblocks(v);
+    return std::max(direct, BPC_BLOCKS);
 }
 
 static double support_r(const VolGeom &v)
@@ -342,13 +499,15 @@ static int bp_rows_needed(const VolGeom &v, const DetGeom &d)
     const double umax = 0.5 * (d.nu - 1) * d.du;
     const double lxy_max = sqrt((double)d.sdd * d.sdd + umax * umax);
     const double sc_min = (d.sad - R) * d.dv / (lxy_max * v.dz);
-    return (int)floor(2.0 / sc_min) + 2;
+    // rows strictly inside (q - m, q + m): at most floor(2m) + 1; the 1e-4
+    // slack covers the FP32 evaluation of m on the device
+    return (int)floor(2.0 / sc_min * (1.0 + 1e-4)) + 1;
 }
 
 static int bp_nr_variant(const VolGeom &v, const DetGeom &d)
 {
     const int need = bp_rows_needed(v, d);
-    for (int nr : {6, 12, 24})
+    for (int nr : {4, 5, 6, 8, 10, 12, 16, 20, 24})
         if (need <= nr) return nr;
     return 0;
 }
@@ -362,7 +521,7 @@ size_t bp_smem_bytes(const VolGeom &v, const DetGeom &d)
     const double m_max = d.sdd / (d.sad - R), m_min = d.sdd / (d.sad + R);
     const double diag = sqrt(pow((BP_TX + 1) * (double)v.dx, 2) + pow((BP_TY + 1) * (double)v.dy, 2));
     const double w = std::min(diag * m_max / d.du + 6.0, (double)d.nu);
-    const double zext = (BP_TZ + 1) * (double)v.dz;
+    const double zext = (32 * bp_zc(v) + 1) * (double)v.dz;
     const double zabs = 0.5 * (v.nz + 1) * v.dz;
     const int nr = bp_nr_variant(v, d);
     const double h = std::min((zext * m_max + zabs * (m_max - m_min)) / d.dv + 6.0, (double)d.nv) + 2.0 * nr + 1;
@@ -372,67 +531,144 @@ size_t bp_smem_bytes(const VolGeom &v, const DetGeom &d)
     return (size_t)cap * sizeof(float);
 }
 
-template <int MODE, bool P, int NR>
-static cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const VolGeom &v,
-                              const DetGeom &d, const float *sino, const float *f, float *out,
-                              const double *d_scale, double scale_val, double kappa, double *partials, int cap,
-                              int pad)
+// out = epilogue(sum over view groups g of part[g]) in a fixed order
+template <int MODE>
+__global__ void __launch_bounds__(BPC_THREADS)
+bp_combine_kernel(const float *__restrict__ part, int groups, size_t n, const float *__restrict__ f,
+                  float *__restrict__ out, const double *__restrict__ d_scale, float scale_val, float kappa,
+                  double *__restrict__ partials)
 {
-    cudaError_t e = cudaFuncSetAttribute(bp_kernel<MODE, P, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    bp_kernel<MODE, P, NR><<<grid, block, smem, s>>>(v, d, sino, f, out, d_scale, (float)scale_val, (float)kappa,
-                                                     partials, cap, pad);
-    return cudaGetLastError();
-}
-
-template <int MODE, bool P>
-static cudaError_t launch_nr(int nr, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const VolGeom &v,
-                             const DetGeom &d, const float *sino, const float *f, float *out,
-                             const double *d_scale, double scale_val, double kappa, double *partials, int cap)
-{
-    switch (nr) {
-    case 6:
-        return launch_one<MODE, P, 6>(grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa,
-                                      partials, cap, 6);
-    case 12:
-        return launch_one<MODE, P, 12>(grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa,
-                                       partials, cap, 12);
-    case 24:
-        return launch_one<MODE, P, 24>(grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa,
-                                       partials, cap, 24);
-    default:
-        return launch_one<MODE, P, 0>(grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa,
-                                      partials, cap, 0);
+    __shared__ double red[32];
+    const float scale = (MODE == 1) ? (d_scale ? (float)(*d_scale) : scale_val) : 0.f;
+    float sq = 0.f;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float s = 0.f;
+        for (int gi = 0; gi < groups; ++gi) s += __ldg(part + (size_t)gi * n + i);
+        if (MODE == 0) {
+            out[i] = s;
+        } else if (MODE == 1) {
+            out[i] = __fmaf_rn(-scale, s, __ldg(f + i));
+        } else {
+            const float w = kappa * s;
+            out[i] = w;
+            sq += w * w;
+        }
+    }
+    if (MODE == 2) {
+        DF v[1] = {DF{sq, 0.f}};
+        double tot[1];
+        block_sum_df<1>(v, red, tot);
+        if (threadIdx.x == 0) partials[blockIdx.x] = tot[0];
     }
 }
 
+int bp_partials_count(const VolGeom &v, const DetGeom &d, bool split)
+{
+    if (split && bp_view_groups(v, d) > 1) return BPC_BLOCKS;
+    return ((v.nx + BP_TX - 1) / BP_TX) * ((v.ny + BP_TY - 1) / BP_TY) * bp_zblocks(v);
+}
+
+#endif // BP_MODE_UNIT == 0
+
+template <int MODE, bool P, int NR, int ZC>
+static cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const BpLaunch &L)
+{
+    cudaError_t e = cudaFuncSetAttribute(bp_kernel<MODE, P, NR, ZC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    bp_kernel<MODE, P, NR, ZC><<<grid, block, smem, s>>>(L.v, L.d, L.sino, L.f, L.out, L.d_scale, L.scale_val,
+                                                         L.kappa, L.partials, L.cap, NR, L.zblocks, L.vpg);
+    return cudaGetLastError();
+}
+
+template <int MODE, bool P, int ZC>
+static cudaError_t launch_nr(int nr, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const BpLaunch &L)
+{
+    switch (nr) {
+    case 4: return launch_one<MODE, P, 4, ZC>(grid, block, smem, s, L);
+    case 5: return launch_one<MODE, P, 5, ZC>(grid, block, smem, s, L);
+    case 6: return launch_one<MODE, P, 6, ZC>(grid, block, smem, s, L);
+    case 8: return launch_one<MODE, P, 8, ZC>(grid, block, smem, s, L);
+    case 10: return launch_one<MODE, P, 10, ZC>(grid, block, smem, s, L);
+    case 12: return launch_one<MODE, P, 12, ZC>(grid, block, smem, s, L);
+    case 16: return launch_one<MODE, P, 16, ZC>(grid, block, smem, s, L);
+    case 20: return launch_one<MODE, P, 20, ZC>(grid, block, smem, s, L);
+    case 24: return launch_one<MODE, P, 24, ZC>(grid, block, smem, s, L);
+    default: return launch_one<MODE, P, 0, ZC>(grid, block, smem, s, L);
+    }
+}
+
+// One dispatcher per (mode, prescaled) pair; BP_MODE_UNIT selects which pairs
+// this translation unit instantiates so the variants compile in parallel.
+template <int MODE, bool P>
+cudaError_t bp_dispatch(int zc, int nr, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const BpLaunch &L)
+{
+    if (zc == 1) return launch_nr<MODE, P, 1>(nr, grid, block, smem, s, L);
+    return launch_nr<MODE, P, 2>(nr, grid, block, smem, s, L);
+}
+
+#if BP_MODE_UNIT == 0
+template cudaError_t bp_dispatch<0, false>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
+template cudaError_t bp_dispatch<2, false>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
+#elif BP_MODE_UNIT == 1
+template cudaError_t bp_dispatch<1, true>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
+template cudaError_t bp_dispatch<1, false>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
+#elif BP_MODE_UNIT == 2
+template cudaError_t bp_dispatch<3, true>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
+template cudaError_t bp_dispatch<3, false>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
+#endif
+
+#if BP_MODE_UNIT == 0
 cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, const float *f,
                         float *out, const double *d_scale, double scale_val, double kappa,
-                        double *partials, int mode, int prescaled, cudaStream_t s)
+                        double *partials, int mode, int prescaled, float *split_ws, cudaStream_t s)
 {
-    dim3 grid((v.nx + BP_TX - 1) / BP_TX, (v.ny + BP_TY - 1) / BP_TY, (v.nz + BP_TZ - 1) / BP_TZ);
+    const int zc = bp_zc(v), zblocks = bp_zblocks(v);
+    const int groups = split_ws ? bp_view_groups(v, d) : 1;
+    const int vpg = (d.n_views + groups - 1) / groups;
+    dim3 grid((v.nx + BP_TX - 1) / BP_TX, (v.ny + BP_TY - 1) / BP_TY, zblocks * groups);
     dim3 block(BP_WARPS * 32);
     const size_t smem = bp_smem_bytes(v, d);
     const int cap = (int)(smem / sizeof(float));
     const int nr = bp_nr_variant(v, d);
     const int kid = mode == 1 ? K_BP_STEP : K_BP;
     cudaError_t e;
+    BpLaunch L{v, d, sino, f, out, d_scale, (float)scale_val, (float)kappa, partials, cap, zblocks, vpg};
     launch_begin(kid, s);
-    if (mode == 0)
-        e = launch_nr<0, false>(nr, grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa, partials,
-                                cap);
-    else if (mode == 1 && prescaled)
-        e = launch_nr<1, true>(nr, grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa, partials,
-                               cap);
-    else if (mode == 1)
-        e = launch_nr<1, false>(nr, grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa, partials,
-                                cap);
-    else
-        e = launch_nr<2, false>(nr, grid, block, smem, s, v, d, sino, f, out, d_scale, scale_val, kappa, partials,
-                                cap);
+    if (groups > 1) {
+        BpLaunch Ls = L;
+        Ls.out = split_ws;
+        if (prescaled)
+            e = bp_dispatch<3, true>(zc, nr, grid, block, smem, s, Ls);
+        else
+            e = bp_dispatch<3, false>(zc, nr, grid, block, smem, s, Ls);
+        if (e == cudaSuccess) {
+            note_extra_launch();
+            const size_t n = (size_t)v.nx * v.ny * v.nz;
+            if (mode == 0)
+                bp_combine_kernel<0><<<BPC_BLOCKS, BPC_THREADS, 0, s>>>(split_ws, groups, n, f, out, d_scale,
+                                                                       (float)scale_val, (float)kappa, partials);
+            else if (mode == 1)
+                bp_combine_kernel<1><<<BPC_BLOCKS, BPC_THREADS, 0, s>>>(split_ws, groups, n, f, out, d_scale,
+                                                                       (float)scale_val, (float)kappa, partials);
+            else
+                bp_combine_kernel<2><<<BPC_BLOCKS, BPC_THREADS, 0, s>>>(split_ws, groups, n, f, out, d_scale,
+                                                                       (float)scale_val, (float)kappa, partials);
+            e = cudaGetLastError();
+        }
+    } else if (mode == 0) {
+        e = bp_dispatch<0, false>(zc, nr, grid, block, smem, s, L);
+    } else if (mode == 1 && prescaled) {
+        e = bp_dispatch<1, true>(zc, nr, grid, block, smem, s, L);
+    } else if (mode == 1) {
+        e = bp_dispatch<1, false>(zc, nr, grid, block, smem, s, L);
+    } else {
+        e = bp_dispatch<2, false>(zc, nr, grid, block, smem, s, L);
+    }
     launch_end(kid, s);
     return e;
 }
+#endif // BP_MODE_UNIT == 0
 
 } // namespace cbct

@@ -178,6 +178,7 @@ enum KernelId {
 
 void launch_begin(int kernel, cudaStream_t s);
 void launch_end(int kernel, cudaStream_t s);
+void note_extra_launch();   // a second kernel inside one timed launch_begin/launch_end bracket
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (one per translation unit)
@@ -196,11 +197,17 @@ cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol,
 // scale = *d_scale if given, else scale_val (sino pre-weighted by ds when
 // prescaled != 0); mode 2: out = kappa P^T sino with partials <- sum out^2
 // (power iteration)
-int bp_grid_blocks(const VolGeom &v);
+// (mode 3 internal: raw per-view-group sums). split_ws (may be null) holds
+// bp_split_floats() floats; with it, grids too small for the GPU split their
+// views over blocks and a combine pass adds the groups in a fixed order.
+int bp_grid_blocks(const VolGeom &v);                                    // partial slots to reserve
+int bp_partials_count(const VolGeom &v, const DetGeom &d, bool split);   // partials of a mode-2 launch
+int bp_view_groups(const VolGeom &v, const DetGeom &d);
+size_t bp_split_floats(const VolGeom &v, const DetGeom &d);
 size_t bp_smem_bytes(const VolGeom &v, const DetGeom &d);
 cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, const float *f,
                         float *out, const double *d_scale, double scale_val, double kappa,
-                        double *partials, int mode, int prescaled, cudaStream_t s);
+                        double *partials, int mode, int prescaled, float *split_ws, cudaStream_t s);
 
 // small kernels (misc.cu)
 cudaError_t launch_sum_partials(const double *partials, int n, int stride, int k, double *out,
