@@ -152,6 +152,24 @@ cbct_status cbct_forward_project(const cbct_geometry *geom, const float *d_vol, 
 cbct_status cbct_residual(const cbct_geometry *geom, const float *d_vol, const float *d_y,
                           float *d_r, double *d_sumsq, void *d_ws, size_t ws_bytes, void *stream);
 
+/* cbct_residual without a workspace, for callers that are not allowed to
+ * allocate device memory (the paper has no counterpart of this call). Some
+ * hosts own every device allocation themselves -- a framework memory pool,
+ * an embedded or safety-certified pipeline with a fixed memory budget, code
+ * running where cudaMalloc is forbidden -- and cannot hand out scratch
+ * buffers. Here the FP64 partial sums live in a fixed array inside the
+ * library (CBCT_STATIC_MAX_PARTIALS doubles, 2 MiB, held by every GPU that
+ * loads the library until the process exits), so the call allocates
+ * nothing. The first call on each device looks up that array's device
+ * address; make that first call before any stream capture. All calls share
+ * the one array: calls that may overlap on the GPU (different streams, or
+ * several threads) race and give wrong sums; serialise them. Geometries with
+ * n_views * nu above CBCT_STATIC_MAX_PARTIALS are rejected with
+ * CBCT_ERR_UNSUPPORTED. Results equal cbct_residual's. */
+#define CBCT_STATIC_MAX_PARTIALS 262144
+cbct_status cbct_residual_static(const cbct_geometry *geom, const float *d_vol, const float *d_y,
+                                 float *d_r, double *d_sumsq, void *stream);
+
 /* d_vol = P^T d_sino, the exact transpose of cbct_forward_project (the matrix
  * view of Sec. II.C.2), evaluated per voxel as a gather: no atomics, every
  * voxel written once. Overwrites d_vol. */

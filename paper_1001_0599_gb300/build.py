@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libcbct.so")
 # split over three objects so they compile in parallel
 SOURCES = [("api.cu", "api.o", ()), ("fp.cu", "fp.o", ()), ("bp.cu", "bp0.o", ("-DBP_MODE_UNIT=0",)),
            ("bp.cu", "bp1.o", ("-DBP_MODE_UNIT=1",)), ("bp.cu", "bp2.o", ("-DBP_MODE_UNIT=2",)),
-           ("tv.cu", "tv.o", ()), ("misc.cu", "misc.o", ())]
+           ("tv.cu", "tv.o", ()), ("misc.cu", "misc.o", ()), ("noalloc.cu", "noalloc.o", ())]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -100,6 +100,8 @@ def load() -> ctypes.CDLL:
     L.cbct_forward_project.restype = st
     L.cbct_residual.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
     L.cbct_residual.restype = st
+    L.cbct_residual_static.argtypes = [_P, _P, _P, _P, _P, _P]
+    L.cbct_residual_static.restype = st
     L.cbct_back_project.argtypes = [_P, _P, _P, _P]
     L.cbct_back_project.restype = st
     L.cbct_gradient_step.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
@@ -234,6 +236,12 @@ def cbct_residual(geom: Geometry, vol, y, r, sumsq, ws, stream=None) -> None:
     _check(load().cbct_residual(geom.handle, _f32(vol, "vol"), _f32(y, "y"), _f32(r, "r"),
                                 _f64(sumsq, "sumsq"), _dev(ws, "ws"), ws.numel() * ws.element_size(),
                                 _stream(stream)))
+
+
+def cbct_residual_static(geom: Geometry, vol, y, r, sumsq, stream=None) -> None:
+    """cbct_residual without a workspace (fixed library-owned partial-sum array)."""
+    _check(load().cbct_residual_static(geom.handle, _f32(vol, "vol"), _f32(y, "y"), _f32(r, "r"),
+                                       _f64(sumsq, "sumsq"), _stream(stream)))
 
 
 def cbct_back_project(geom: Geometry, sino, vol, stream=None) -> None:

@@ -861,3 +861,20 @@ extern "C" void cbct_profile_reset(void)
     }
     g_pool_used = 0;
 }
+
+// ---------------------------------------------------------------------------
+// accessors for other translation units
+// ---------------------------------------------------------------------------
+namespace cbct {
+const VolGeom *geometry_level(const cbct_geometry *g, int level)
+{
+    return (g && level >= 0 && level < g->n_levels) ? &g->lev[level].vg : nullptr;
+}
+const DetGeom *geometry_detector(const cbct_geometry *g) { return g ? &g->det : nullptr; }
+int geometry_device(const cbct_geometry *g) { return g ? g->device : -1; }
+cbct_status report_error(cbct_status st, const char *msg)
+{
+    if (st == CBCT_OK) return ok();
+    return fail(st, "%s", msg);
+}
+} // namespace cbct

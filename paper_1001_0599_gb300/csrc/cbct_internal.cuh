@@ -250,4 +250,11 @@ struct RofArgs {
 int rof_grid_blocks();
 cudaError_t launch_rof(const RofArgs &a, cudaStream_t s);
 
+// Read-only views of a geometry handle and error reporting (api.cu), for
+// entry points that live in other translation units.
+const VolGeom *geometry_level(const cbct_geometry *g, int level);
+const DetGeom *geometry_detector(const cbct_geometry *g);
+int geometry_device(const cbct_geometry *g);
+cbct_status report_error(cbct_status st, const char *msg);
+
 } // namespace cbct
