@@ -146,6 +146,35 @@ def oracle_sample(wl, y):
     return t_total, "; ".join(parts)
 
 
+def rank_noise_seed(base_seed: int, rank: int) -> int:
+    """Noise seed of the scan a rank reconstructs: rank 0 keeps the workload's
+    seed, every other rank draws its own noise (independent scans)."""
+    return base_seed if rank == 0 else base_seed + 1000 * rank
+
+
+def job_seconds_per_scan(local_ms: float, scans_per_rank: int, world: int, dist=None, device="cpu") -> float:
+    """Whole-job time per scan: the slowest rank's wall time over all scans of
+    all ranks (max over ranks of the local timed region)."""
+    t = local_ms
+    if dist is not None and world > 1:
+        import torch
+        v = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        t = float(v.item())
+    return t / 1e3 / (scans_per_rank * world)
+
+
+def oracle_sample_warm(wl):
+    """One untimed single-view projection on the finest grid (thread pool and
+    first-touch warm-up before the timed oracle sample)."""
+    import numpy as np
+    from oracle import oracle as orc
+    g = orc.Geometry.from_workload(wl)
+    sub = orc.Geometry(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.nu, g.nv, g.du, g.dv, g.sad, g.sdd,
+                       g.angles[:1].copy(), g.step_ratio)
+    orc.back_project(sub, orc.forward_project(sub, np.ones(g.vol_shape)))
+
+
 def cpu_cores():
     try:
         return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count())
@@ -206,7 +235,7 @@ def main():
     truth, y = synthetic.make_problem(wl)
     if world > 1:  # each rank reconstructs its own scan (different noise draw)
         y = synthetic.poisson_log_sinogram(synthetic.exact_sinogram(synthetic.make_phantom(wl), wl),
-                                           wl.photons, wl.noise_seed + 1000 * rank)
+                                           wl.photons, rank_noise_seed(wl.noise_seed, rank))
     g = cbct.geometry_from_workload(wl)
     tv = cbct.TvParams.paper(eps_tv=1e-5)
     if args.mode == "one-iteration":
@@ -261,12 +290,8 @@ def main():
     launches = cbct.cbct_launch_count() - n0 - 0
     cbct.cbct_profile_enable(False)
     prof = cbct.cbct_profile_query()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    sec_per_scan = total_ms / 1e3 / (args.steps * world)
+    sec_per_scan = job_seconds_per_scan(sum(step_ms), args.steps, world, dist, "cuda")
+    total_ms = sec_per_scan * 1e3 * args.steps * world
     st = cbct.read_stats(stats)
     recon = vol.cpu().numpy().astype(np.float64)
     rel_err = float(np.linalg.norm(recon - truth) / np.linalg.norm(truth))
@@ -286,12 +311,8 @@ def main():
         for _ in range(args.steps):
             flush.zero_()
             cbct.cbct_reconstruct_host(g, h_y.numpy(), h_vol.numpy(), params, ws_h)
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": e2e_s / (args.steps * world), "unit": "s",
+        e2e_per_scan = job_seconds_per_scan((time.perf_counter() - t0) * 1e3, args.steps, world, dist, "cuda")
+        e2e = {"value": e2e_per_scan, "unit": "s",
                "h2d_bytes_per_step": int(h_y.numel() * 4), "d2h_bytes_per_step": int(h_vol.numel() * 4)}
         del ws_h
 
@@ -336,6 +357,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as orc
         orc.build()
+        oracle_sample_warm(wl)
         v, sample = oracle_sample(wl, y)
         line["cpu_baseline"] = {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
                                 "sample": sample + " (scaled to one reconstruction)"}
