@@ -18,10 +18,10 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcbct.so")
 # (source, object, extra nvcc flags): the transpose's template variants are
-# split over three objects so they compile in parallel
-SOURCES = [("api.cu", "api.o", ()), ("fp.cu", "fp.o", ()), ("bp.cu", "bp0.o", ("-DBP_MODE_UNIT=0",)),
-           ("bp.cu", "bp1.o", ("-DBP_MODE_UNIT=1",)), ("bp.cu", "bp2.o", ("-DBP_MODE_UNIT=2",)),
-           ("tv.cu", "tv.o", ()), ("misc.cu", "misc.o", ()), ("noalloc.cu", "noalloc.o", ())]
+# split over six objects so they compile in parallel
+SOURCES = [("api.cu", "api.o", ()), ("fp.cu", "fp.o", ())] + \
+    [("bp.cu", f"bp{u}.o", (f"-DBP_MODE_UNIT={u}",)) for u in range(6)] + \
+    [("tv.cu", "tv.o", ()), ("misc.cu", "misc.o", ()), ("noalloc.cu", "noalloc.o", ())]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -291,6 +291,8 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
         v.cz = (float)(0.5 * (nz - 1));
         v.drho = (float)drho;
         v.cols = L.d_cols;
+        v.bp_cap = 0;
+        v.bp_cap = bp_patch_floats(v, det, d.angles);
         L.drho = drho;
         L.dx = dx;
         L.dy = dy;
@@ -651,8 +653,9 @@ static cbct_status run_power(const cbct_geometry *G, int level, int n_iter, void
     CUDA_TRY(launch_power_init(st, (double)nvox(v), s));
     CUDA_TRY(launch_fill(w, nvox(v), 1.f, s));
     for (int it = 0; it < n_iter; it++) {
-        CUDA_TRY(launch_forward(v, G->det, w, nullptr, sino, &st->inv_wnorm, nullptr, 0, s));
-        CUDA_TRY(launch_back(v, G->det, sino, nullptr, w, nullptr, 0.0, kappa, partials, 2, 0,
+        // projection pre-weighted by ds (mode 3) feeds the transpose's staged patch directly
+        CUDA_TRY(launch_forward(v, G->det, w, nullptr, sino, &st->inv_wnorm, nullptr, 3, s));
+        CUDA_TRY(launch_back(v, G->det, sino, nullptr, w, nullptr, 0.0, kappa, partials, 2, 1,
                              at<float>(ws, L.split), s));
         CUDA_TRY(launch_power_update(st, partials, bp_partials_count(v, G->det, true), kappa, it == 0,
                                      it == n_iter - 1, d_L_out, s));

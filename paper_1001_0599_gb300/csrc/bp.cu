@@ -52,6 +52,11 @@ struct __align__(16) SampleEntry {
 };
 constexpr int BP_ENTRIES = 96;    // entries per warp and batch
 
+// Warps per column group for a row count NR: voxels whose z tent spans many
+// detector rows come with tall staged patches and so with few blocks per SM;
+// more warps per group then keep the SM busy.
+__host__ __device__ constexpr int bp_split_for(int nr) { return (nr == 0 || nr > 16) ? 4 : (nr > 8 ? 2 : 1); }
+
 struct BpLaunch {
     VolGeom v;
     DetGeom d;
@@ -62,6 +67,7 @@ struct BpLaunch {
     float scale_val, kappa;
     double *partials;
     int cap, zblocks, vpg;
+    int split;   // warps per column group
 };
 
 template <int MODE, bool P>
@@ -183,24 +189,30 @@ __device__ __forceinline__ void add_corners(float (&acc)[BP_G][BP_G][ZC], float 
 }
 
 // NR > 0: rows per (lane, sample) fully unrolled; NR == 0: runtime loop.
-// Block: BP_WARPS warps, each owning a BP_G x BP_G group of voxel columns and
-// the block's 32*ZC z values (one per lane and chunk). With a view split
-// (MODE 3) block z index = z block + zblocks * view group, and the block adds
-// only its group's views and writes the raw sums to out + group * N_vox.
-template <int MODE, bool PRESCALED, int NR, int ZC>
-__global__ void __launch_bounds__(BP_WARPS * 32)
+// Block: BP_WARPS x SPLIT warps. Warp w owns the BP_G x BP_G group of voxel
+// columns w % BP_WARPS and the block's 32*ZC z values (one per lane and
+// chunk); the SPLIT warps of a group take every SPLIT-th sample of its
+// footprint and add their sums at the end (coarse grids, whose large detector
+// patches leave room for few blocks per SM). With a view split (MODE 3) block z
+// index = z block + zblocks * view group, and the block adds only its group's
+// views and writes the raw sums to out + group * N_vox.
+template <int MODE, bool PRESCALED, int NR, int ZC, int SPLIT>
+__global__ void __launch_bounds__(BP_WARPS * 32 * SPLIT, SPLIT == 1 ? 5 : (SPLIT == 2 ? 2 : 1))
 bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__restrict__ f,
           float *__restrict__ out, const double *__restrict__ d_scale, float scale_val, float kappa,
           double *__restrict__ partials, int patch_cap, int pad, int zblocks, int views_per_group)
 {
     constexpr int BP_ZC = ZC;
     constexpr int BP_TZ = 32 * ZC;
+    constexpr int NWARPS = BP_WARPS * SPLIT;
+    constexpr int NENT = BP_ENTRIES / SPLIT;   // list slots per warp and batch
     extern __shared__ float patch[];
     __shared__ int s_box[6];
     __shared__ double red[32];
     __shared__ SampleEntry s_ent[BP_WARPS * BP_ENTRIES];
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int warp = wid % BP_WARPS, part = wid / BP_WARPS;
     const int zb = (int)blockIdx.z % zblocks, vg = (int)blockIdx.z / zblocks;
     const int a_base = blockIdx.x * BP_TX, b_base = blockIdx.y * BP_TY, c_base = zb * BP_TZ;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nu = d.nu, nv = d.nv;
@@ -259,7 +271,7 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
         if (staged) {
             const int w = iu1 - iu0 + 1, h = s1 - s0 + 1;
             const float *src = sino + (size_t)view * nv * nu;
-            for (int r = warp; r < h; r += BP_WARPS) {
+            for (int r = wid; r < h; r += NWARPS) {
                 const int iv = s0 + r;
                 const bool in = iv >= 0 && iv < nv;
                 for (int cc = lane; cc < w; cc += 32) {
@@ -284,7 +296,7 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
             box_u_range(d, cs.x, cs.y, gbox, ju0, ju1, dlo, dhi);
             ju0 = max(ju0, iu0);
             ju1 = min(ju1, iu1);
-            SampleEntry *ent = s_ent + warp * BP_ENTRIES;
+            SampleEntry *ent = s_ent + wid * NENT;
             const float inv_drho = fast_rcp(g.drho);
             // lanes take detector columns; each enumerates its line's samples in
             // the group's footprint (entries ordered by column, then sample)
@@ -328,10 +340,11 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
                 const int first = incl - cnt;
                 const float sc_base = d.dv * rc.inv_lxy * g.inv_dz;
                 const int col_off = (iu - iu0) * hp - s0;
-                for (int b0 = 0; b0 < total; b0 += BP_ENTRIES) {
-                    // fill this batch's entries
-                    const int lo = max(first, b0), hi = min(first + cnt, b0 + BP_ENTRIES);
+                for (int b0 = 0; b0 < total; b0 += NENT * SPLIT) {
+                    // fill this warp's entries of the batch window (every SPLIT-th one)
+                    const int lo = max(first, b0), hi = min(first + cnt, b0 + NENT * SPLIT);
                     for (int e = lo; e < hi; ++e) {
+                        if (SPLIT > 1 && (e - b0) % SPLIT != part) continue;
                         const int j = jl + (e - first);
                         float fx, fy;
                         sample_xy(g, rc, j, fx, fy);
@@ -351,10 +364,11 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
                         en.w11 = wx1 * wy1;
                         en.sc = sc;
                         en.m = fast_rcp(sc);
-                        ent[e - b0] = en;
+                        ent[(e - b0) / SPLIT] = en;
                     }
                     __syncwarp();
-                    const int nb = min(BP_ENTRIES, total - b0);
+                    const int nwin = min(NENT * SPLIT, total - b0);
+                    const int nb = (nwin - part + SPLIT - 1) / SPLIT;
                     for (int e = 0; e < nb; ++e) {
                         const SampleEntry en = ent[e];
                         if (en.cell < 0) continue;  // uniform
@@ -404,7 +418,34 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
         __syncthreads();
     }
 
-    // epilogue: one write per voxel
+    if (SPLIT > 1) {
+        // add the other parts' sums into part 0 (the patch is free now)
+        float *xch = patch;   // [SPLIT-1][BP_WARPS][BP_G*BP_G*ZC][32]
+        constexpr int PER = BP_G * BP_G * ZC;
+        if (part > 0) {
+            float *dst = xch + ((size_t)(part - 1) * BP_WARPS + warp) * PER * 32;
+#pragma unroll
+            for (int ia = 0; ia < BP_G; ++ia)
+#pragma unroll
+                for (int ib = 0; ib < BP_G; ++ib)
+#pragma unroll
+                    for (int zc = 0; zc < ZC; ++zc) dst[((ia * BP_G + ib) * ZC + zc) * 32 + lane] = acc[ia][ib][zc];
+        }
+        __syncthreads();
+        if (part == 0) {
+            for (int pp = 1; pp < SPLIT; ++pp) {
+                const float *src = xch + ((size_t)(pp - 1) * BP_WARPS + warp) * PER * 32;
+#pragma unroll
+                for (int ia = 0; ia < BP_G; ++ia)
+#pragma unroll
+                    for (int ib = 0; ib < BP_G; ++ib)
+#pragma unroll
+                        for (int zc = 0; zc < ZC; ++zc) acc[ia][ib][zc] += src[((ia * BP_G + ib) * ZC + zc) * 32 + lane];
+            }
+        }
+    }
+
+    // epilogue: one write per voxel (part-0 warps)
     const float scale = (MODE == 1) ? (d_scale ? (float)(*d_scale) : scale_val) : 0.f;
     float sq = 0.f;
 #pragma unroll
@@ -412,6 +453,7 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
 #pragma unroll
         for (int ib = 0; ib < BP_G; ++ib) {
             const int a = A + ia, b = B + ib;
+            if (part != 0) continue;
             if (a >= nx || b >= ny) continue;
 #pragma unroll
             for (int zc = 0; zc < BP_ZC; ++zc) {
@@ -512,10 +554,61 @@ static int bp_nr_variant(const VolGeom &v, const DetGeom &d)
     return 0;
 }
 
-// Upper bound of the staged patch (host side, FP64, mirrors the device box
-// computation with slack); tiles that still do not fit fall back to reading
-// the sinogram from global memory.
+// Largest staged patch (floats) of any block and view on this grid: a host
+// mirror (FP64) of the device's box computation, with two pixels of slack on
+// each side. Blocks whose patch still does not fit read the sinogram from
+// global memory instead.
+int bp_patch_floats(const VolGeom &v, const DetGeom &d, const double *angles)
+{
+    const int zc = bp_zc(v), tz = 32 * zc, nr = bp_nr_variant(v, d);
+    const int nbx = (v.nx + BP_TX - 1) / BP_TX, nby = (v.ny + BP_TY - 1) / BP_TY, nbz = bp_zblocks(v);
+    const double cx = 0.5 * (v.nx - 1), cy = 0.5 * (v.ny - 1), cz = 0.5 * (v.nz - 1);
+    const double cu = 0.5 * (d.nu - 1), cv = 0.5 * (d.nv - 1);
+    long best = 0;
+    for (int k = 0; k < d.n_views; k++) {
+        const double c = cos(angles[k]), sn = sin(angles[k]);
+        for (int bx = 0; bx < nbx; bx++)
+            for (int by = 0; by < nby; by++) {
+                const double x0 = (bx * BP_TX - cx) * v.dx - v.dx, x1 = (bx * BP_TX - cx) * v.dx + BP_TX * v.dx;
+                const double y0 = (by * BP_TY - cy) * v.dy - v.dy, y1 = (by * BP_TY - cy) * v.dy + BP_TY * v.dy;
+                double umin = 1e300, umax = -1e300, xrlo = 1e300, xrhi = -1e300;
+                for (int q = 0; q < 4; q++) {
+                    const double x = (q & 1) ? x1 : x0, y = (q & 2) ? y1 : y0;
+                    const double xr = x * c + y * sn, yr = -x * sn + y * c;
+                    const double u = -yr * d.sdd / (xr + d.sad);
+                    umin = std::min(umin, u);
+                    umax = std::max(umax, u);
+                    xrlo = std::min(xrlo, xr);
+                    xrhi = std::max(xrhi, xr);
+                }
+                const int iu0 = std::max((int)floor(umin / d.du + cu) - 3, 0);
+                const int iu1 = std::min((int)ceil(umax / d.du + cu) + 3, d.nu - 1);
+                const double mn = d.sdd / (xrlo + d.sad), mf = d.sdd / (xrhi + d.sad);
+                for (int bz = 0; bz < nbz; bz++) {
+                    const double zlo = (bz * tz - cz - 1.0) * v.dz, zhi = (bz * tz + tz - cz) * v.dz;
+                    const double vmin = std::min(std::min(zlo * mn, zlo * mf), std::min(zhi * mn, zhi * mf));
+                    const double vmax = std::max(std::max(zlo * mn, zlo * mf), std::max(zhi * mn, zhi * mf));
+                    const int iv0 = std::max((int)floor(vmin / d.dv + cv) - 3, 0);
+                    const int iv1 = std::min((int)ceil(vmax / d.dv + cv) + 3, d.nv - 1);
+                    if (iu1 < iu0 || iv1 < iv0) continue;
+                    const long w = iu1 - iu0 + 1, h = (iv1 - iv0 + 1) + 2L * nr;
+                    best = std::max(best, w * (h | 1));
+                }
+            }
+    }
+    const long cap_max = 48L * 1024L;   // floats: 192 KB
+    return (int)std::min(best, cap_max);
+}
+
+// Dynamic shared memory of a transpose launch on this grid.
 size_t bp_smem_bytes(const VolGeom &v, const DetGeom &d)
+{
+    if (v.bp_cap > 0) return (size_t)v.bp_cap * sizeof(float);
+    return bp_smem_bound(v, d);
+}
+
+// Analytic upper bound of the staged patch (used when no exact size is known).
+size_t bp_smem_bound(const VolGeom &v, const DetGeom &d)
 {
     const double R = support_r(v);
     const double m_max = d.sdd / (d.sad - R), m_min = d.sdd / (d.sad + R);
@@ -571,15 +664,29 @@ int bp_partials_count(const VolGeom &v, const DetGeom &d, bool split)
 
 #endif // BP_MODE_UNIT == 0
 
+template <int MODE, bool P, int NR, int ZC, int SPLIT>
+static cudaError_t launch_split(dim3 grid, size_t smem, cudaStream_t s, const BpLaunch &L)
+{
+    // the parts' exchange at the end reuses the patch buffer
+    const size_t xch = (size_t)(SPLIT - 1) * BP_WARPS * BP_G * BP_G * ZC * 32 * sizeof(float);
+    if (xch > smem) smem = xch;
+    cudaError_t e = cudaFuncSetAttribute(bp_kernel<MODE, P, NR, ZC, SPLIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // the staged patches, not L1, hold the reused data: ask for the largest carveout
+    e = cudaFuncSetAttribute(bp_kernel<MODE, P, NR, ZC, SPLIT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    bp_kernel<MODE, P, NR, ZC, SPLIT><<<grid, BP_WARPS * 32 * SPLIT, smem, s>>>(
+        L.v, L.d, L.sino, L.f, L.out, L.d_scale, L.scale_val, L.kappa, L.partials, L.cap, NR, L.zblocks, L.vpg);
+    return cudaGetLastError();
+}
+
 template <int MODE, bool P, int NR, int ZC>
 static cudaError_t launch_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const BpLaunch &L)
 {
-    cudaError_t e = cudaFuncSetAttribute(bp_kernel<MODE, P, NR, ZC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    bp_kernel<MODE, P, NR, ZC><<<grid, block, smem, s>>>(L.v, L.d, L.sino, L.f, L.out, L.d_scale, L.scale_val,
-                                                         L.kappa, L.partials, L.cap, NR, L.zblocks, L.vpg);
-    return cudaGetLastError();
+    (void)block;
+    return launch_split<MODE, P, NR, ZC, bp_split_for(NR)>(grid, smem, s, L);
 }
 
 template <int MODE, bool P, int ZC>
@@ -610,12 +717,15 @@ cudaError_t bp_dispatch(int zc, int nr, dim3 grid, dim3 block, size_t smem, cuda
 
 #if BP_MODE_UNIT == 0
 template cudaError_t bp_dispatch<0, false>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
-template cudaError_t bp_dispatch<2, false>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
 #elif BP_MODE_UNIT == 1
 template cudaError_t bp_dispatch<1, true>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
-template cudaError_t bp_dispatch<1, false>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
 #elif BP_MODE_UNIT == 2
+template cudaError_t bp_dispatch<1, false>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
+#elif BP_MODE_UNIT == 3
+template cudaError_t bp_dispatch<2, true>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
+#elif BP_MODE_UNIT == 4
 template cudaError_t bp_dispatch<3, true>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
+#elif BP_MODE_UNIT == 5
 template cudaError_t bp_dispatch<3, false>(int, int, dim3, dim3, size_t, cudaStream_t, const BpLaunch &);
 #endif
 
@@ -634,7 +744,8 @@ cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, c
     const int nr = bp_nr_variant(v, d);
     const int kid = mode == 1 ? K_BP_STEP : K_BP;
     cudaError_t e;
-    BpLaunch L{v, d, sino, f, out, d_scale, (float)scale_val, (float)kappa, partials, cap, zblocks, vpg};
+    const int split = bp_split_for(nr);
+    BpLaunch L{v, d, sino, f, out, d_scale, (float)scale_val, (float)kappa, partials, cap, zblocks, vpg, split};
     launch_begin(kid, s);
     if (groups > 1) {
         BpLaunch Ls = L;
@@ -663,8 +774,10 @@ cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, c
         e = bp_dispatch<1, true>(zc, nr, grid, block, smem, s, L);
     } else if (mode == 1) {
         e = bp_dispatch<1, false>(zc, nr, grid, block, smem, s, L);
+    } else if (prescaled) {
+        e = bp_dispatch<2, true>(zc, nr, grid, block, smem, s, L);   // power iteration: ds-weighted input
     } else {
-        e = bp_dispatch<2, false>(zc, nr, grid, block, smem, s, L);
+        e = cudaErrorInvalidValue;   // the power-iteration transpose takes a ds-weighted sinogram
     }
     launch_end(kid, s);
     return e;

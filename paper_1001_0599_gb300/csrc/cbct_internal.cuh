@@ -36,6 +36,7 @@ struct VolGeom {
     float cx, cy, cz;          // (n - 1) / 2
     float drho;                // in-plane sample spacing
     const RayCol *cols;        // [n_views][nu]
+    int bp_cap;                // largest staged detector patch of the transpose, floats (0: bound)
 };
 
 struct DetGeom {
@@ -187,6 +188,7 @@ void note_extra_launch();   // a second kernel inside one timed launch_begin/lau
 // forward projector. mode 0: out = scale * P vol (scale from d_scale if given)
 // mode 1: out = P vol - y (unscaled residual), partials <- sum r^2
 // mode 2: out = ds * (P vol - y) (residual pre-weighted for the transpose), partials <- sum r^2
+// mode 3: out = scale * ds * P vol (projection pre-weighted for the transpose)
 int fp_grid_blocks(const DetGeom &d);                          // largest grid (workspace sizing)
 int fp_partials_count(const VolGeom &v, const DetGeom &d);      // blocks of the launch for this level
 cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
@@ -205,6 +207,8 @@ int bp_partials_count(const VolGeom &v, const DetGeom &d, bool split);   // part
 int bp_view_groups(const VolGeom &v, const DetGeom &d);
 size_t bp_split_floats(const VolGeom &v, const DetGeom &d);
 size_t bp_smem_bytes(const VolGeom &v, const DetGeom &d);
+int bp_patch_floats(const VolGeom &v, const DetGeom &d, const double *angles);
+size_t bp_smem_bound(const VolGeom &v, const DetGeom &d);
 cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, const float *f,
                         float *out, const double *d_scale, double scale_val, double kappa,
                         double *partials, int mode, int prescaled, float *split_ws, cudaStream_t s);

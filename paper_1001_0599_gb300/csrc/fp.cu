@@ -32,7 +32,7 @@ fp_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__re
 {
     constexpr int ROWS = 32 * RPL;
     __shared__ float tile[ROWS][FP_WARPS + 1];
-    __shared__ float tile_ds[MODE == 2 ? ROWS : 1][FP_WARPS + 1];
+    __shared__ float tile_ds[(MODE == 2 || MODE == 3) ? ROWS : 1][FP_WARPS + 1];
     __shared__ float hbuf[FP_WARPS][FP_HMAX + 2];
     __shared__ double red[32];
 
@@ -143,13 +143,13 @@ fp_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__re
 #pragma unroll
     for (int k = 0; k < RPL; k++) {
         tile[lane + 32 * k][warp] = acc[k] * ds[k];
-        if (MODE == 2) tile_ds[lane + 32 * k][warp] = ds[k];
+        if (MODE == 2 || MODE == 3) tile_ds[lane + 32 * k][warp] = ds[k];
     }
     __syncthreads();
 
     // transposed write-back: ROWS rows x 8 consecutive columns
     float r2 = 0.f;
-    const float scale = (MODE == 0 && d_scale) ? (float)(*d_scale) : 1.f;
+    const float scale = ((MODE == 0 || MODE == 3) && d_scale) ? (float)(*d_scale) : 1.f;
     for (int e = threadIdx.x; e < ROWS * FP_WARPS; e += FP_WARPS * 32) {
         const int row = e >> 3, col = e & 7;
         const int oiv = row0 + row, oiu = blockIdx.x * FP_WARPS + col;
@@ -158,6 +158,8 @@ fp_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__re
             const float p = tile[row][col];
             if (MODE == 0) {
                 out[o] = p * scale;
+            } else if (MODE == 3) {
+                out[o] = p * scale * tile_ds[row][col];
             } else {
                 const float r = p - __ldg(y + o);
                 r2 += r * r;
@@ -165,7 +167,7 @@ fp_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__re
             }
         }
     }
-    if (MODE != 0) {
+    if (MODE == 1 || MODE == 2) {
         DF v[1] = {DF{r2, 0.f}};
         double tot[1];
         block_sum_df<1>(v, red, tot);
@@ -277,11 +279,26 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float
                         w3 * __ldg(vol + o3 + c);
         }
         __syncthreads();
+        // 32-row bands whose rows stay outside the volume over the whole chunk
+        // (rows above the top or below the bottom for every sample) are skipped
+        bool band[RT];
+        {
+            const float ra = s_rho[0], rb = s_rho[nj - 1];
+#pragma unroll
+            for (int k = 0; k < RT; k++) {
+                const float t_lo = __shfl_sync(0xffffffffu, tz[k], 0), t_hi = __shfl_sync(0xffffffffu, tz[k], 31);
+                const float z1 = __fmaf_rn(ra, t_lo, g.cz), z2 = __fmaf_rn(rb, t_lo, g.cz);
+                const float z3 = __fmaf_rn(ra, t_hi, g.cz), z4 = __fmaf_rn(rb, t_hi, g.cz);
+                const float zlo = fminf(fminf(z1, z2), fminf(z3, z4)), zhi = fmaxf(fmaxf(z1, z2), fmaxf(z3, z4));
+                band[k] = !(zhi < -1.f || zlo >= (float)nz);
+            }
+        }
         for (int jj = 0; jj < nj; ++jj) {
             const float rho = s_rho[jj];
             const float *Hr = H + jj * hs + 2;
 #pragma unroll
             for (int k = 0; k < RT; k++) {
+                if (!band[k]) continue;
                 const float zeta = __fmaf_rn(rho, tz[k], g.cz);
                 const float c0f = floorf(zeta);
                 const int c0 = clampi((int)c0f, -2, nz);
@@ -294,7 +311,7 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float
     }
 
     float r2 = 0.f;
-    const float scale = (MODE == 0 && d_scale) ? (float)(*d_scale) : 1.f;
+    const float scale = ((MODE == 0 || MODE == 3) && d_scale) ? (float)(*d_scale) : 1.f;
 #pragma unroll
     for (int k = 0; k < RT; k++) {
         const int iv = tid + FS_THREADS * k;
@@ -303,6 +320,8 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float
             const float p = acc[k] * ds[k];
             if (MODE == 0) {
                 out[o] = p * scale;
+            } else if (MODE == 3) {
+                out[o] = p * scale * ds[k];
             } else {
                 const float r = p - __ldg(y + o);
                 r2 += r * r;
@@ -310,7 +329,7 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float
             }
         }
     }
-    if (MODE != 0) {
+    if (MODE == 1 || MODE == 2) {
         DF v[1] = {DF{r2, 0.f}};
         double tot[1];
         block_sum_df<1>(v, red, tot);
@@ -399,13 +418,15 @@ cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol,
                            float *out, const double *d_scale, double *partials, int mode,
                            cudaStream_t s)
 {
-    const int kid = mode == 0 ? K_FP : K_FP_RESID;
+    const int kid = (mode == 0 || mode == 3) ? K_FP : K_FP_RESID;
     const int rt = fp_sheet_rows(v, d);
     if (rt > 0) {
         launch_begin(kid, s);
         cudaError_t e;
         if (mode == 0)
             e = launch_sheet<0>(rt, v, d, vol, y, out, d_scale, partials, s);
+        else if (mode == 3)
+            e = launch_sheet<3>(rt, v, d, vol, y, out, d_scale, partials, s);
         else if (mode == 1)
             e = launch_sheet<1>(rt, v, d, vol, y, out, d_scale, partials, s);
         else
@@ -417,6 +438,8 @@ cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol,
     launch_begin(kid, s);
     if (mode == 0)
         launch_mode<0>(v, d, vol, y, out, d_scale, partials, rpl, s);
+    else if (mode == 3)
+        launch_mode<3>(v, d, vol, y, out, d_scale, partials, rpl, s);
     else if (mode == 1)
         launch_mode<1>(v, d, vol, y, out, d_scale, partials, rpl, s);
     else
