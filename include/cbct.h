@@ -93,8 +93,11 @@ typedef struct {
     int n_levels;                    /* multigrid levels, 1..CBCT_MAX_LEVELS (Sec. II.C.3) */
     int iters[CBCT_MAX_LEVELS];      /* FBS iterations per level, coarsest first */
     double tau[CBCT_MAX_LEVELS];     /* step per level (mean metric); <= 0: 1/L by power iteration */
-    int power_iters;                 /* power iterations for L (0 -> 20) */
+    int power_iters;                 /* power iterations for L (0 -> 20), started from ones */
     int clamp;                       /* apply Step 3 of Algorithm A1 (f >= 0) */
+    int power_iters_fine;            /* > 0: every level after the first runs this many power
+                                        iterations started from the prolongation of the previous
+                                        level's last iterate instead of power_iters from ones */
     cbct_tv_params tv;
     /* Optional replay of a recorded step schedule (testing): host array of
      * records, one per FBS iteration in order: n, then n step-reduction

@@ -467,16 +467,14 @@ int orc_fbs_iteration(const orc_geom *g, const double *y, double *f, double lamb
     return rc;
 }
 
-double orc_power_lipschitz(const orc_geom *g, int n_iter)
+double orc_power_lipschitz_from(const orc_geom *g, double *v, int n_iter)
 {
     const size_t n = (size_t)g->nx * g->ny * g->nz;
     const size_t m = (size_t)g->n_views * g->nv * g->nu;
     const double kappa = 2.0 * (double)n / (double)m;
-    double *v = (double *)malloc(n * sizeof(double));
     double *w = (double *)malloc(n * sizeof(double));
     double *s = (double *)malloc(m * sizeof(double));
     double L = 0.0;
-    for (size_t j = 0; j < n; j++) v[j] = 1.0;
     for (int it = 0; it < n_iter; it++) {
         orc_forward_project(g, v, s);
         orc_back_project(g, s, w);
@@ -490,9 +488,18 @@ double orc_power_lipschitz(const orc_geom *g, int n_iter)
         double inv = 1.0 / sqrt(nw2);
         for (size_t j = 0; j < n; j++) v[j] = w[j] * inv;
     }
-    free(v);
     free(w);
     free(s);
+    return L;
+}
+
+double orc_power_lipschitz(const orc_geom *g, int n_iter)
+{
+    const size_t n = (size_t)g->nx * g->ny * g->nz;
+    double *v = (double *)malloc(n * sizeof(double));
+    for (size_t j = 0; j < n; j++) v[j] = 1.0;
+    const double L = orc_power_lipschitz_from(g, v, n_iter);
+    free(v);
     return L;
 }
 

@@ -109,6 +109,9 @@ int orc_fbs_iteration(const orc_geom *g, const double *y, double *f, double lamb
 
 /* Lipschitz constant of kappa P^T P by power iteration from v = 1. */
 double orc_power_lipschitz(const orc_geom *g, int n_iter);
+/* Same from the start vector v (any scale); on return v holds the last
+ * normalised iterate. */
+double orc_power_lipschitz_from(const orc_geom *g, double *v, int n_iter);
 
 /* Cell-centred trilinear prolongation from (nx/2, ny/2, nz/2) to (nx, ny, nz),
  * clamp to edge (Sec. II.C.3). */

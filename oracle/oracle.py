@@ -93,6 +93,8 @@ def lib():
                                         _I, ctypes.c_int, ctypes.POINTER(_RofStats), _D]
         L.orc_power_lipschitz.argtypes = [G, ctypes.c_int]
         L.orc_power_lipschitz.restype = ctypes.c_double
+        L.orc_power_lipschitz_from.argtypes = [G, _D, ctypes.c_int]
+        L.orc_power_lipschitz_from.restype = ctypes.c_double
         L.orc_prolong.argtypes = [ctypes.c_int] * 3 + [_D, _D]
         _lib = L
     return _lib
@@ -294,6 +296,13 @@ def power_lipschitz(g: Geometry, n_iter: int = 20) -> float:
     return lib().orc_power_lipschitz(ctypes.byref(g._c()), n_iter)
 
 
+def power_lipschitz_from(g: Geometry, v, n_iter: int):
+    """Power iteration from start vector v; returns (L, last normalised iterate)."""
+    v = _f64(v).copy()
+    L = lib().orc_power_lipschitz_from(ctypes.byref(g._c()), _dp(v), n_iter)
+    return L, v
+
+
 def prolong(coarse) -> np.ndarray:
     coarse = _f64(coarse)
     ncx, ncy, ncz = coarse.shape
@@ -345,7 +354,8 @@ class ReconResult:
 def reconstruct(g: Geometry, y, lam: float, iters: Sequence[int], p: TVParams,
                 taus: Optional[Sequence[float]] = None, power_iters: int = 20,
                 clamp: bool = True, f_init=None,
-                replay: Optional[Sequence[Sequence[int]]] = None) -> ReconResult:
+                replay: Optional[Sequence[Sequence[int]]] = None,
+                power_iters_fine: int = 0) -> ReconResult:
     """Algorithm A1 under the coarse-to-fine schedule of Sec. II.C.3.
 
     ``iters`` lists the FBS iterations per level, coarsest first; level l of
@@ -353,13 +363,17 @@ def reconstruct(g: Geometry, y, lam: float, iters: Sequence[int], p: TVParams,
     coarsest level starts from ``f_init`` (default zero); each later level
     starts from the trilinear prolongation of the previous result. The step
     tau of each level is ``taus[l]`` when given, else 1/L from ``power_iters``
-    power iterations on kappa P^T P.
+    power iterations on kappa P^T P started from ones; with
+    ``power_iters_fine`` > 0, every level after the first instead runs that
+    many iterations started from the prolongation of the previous level's
+    last iterate.
     """
     y = _f64(y)
     n_levels = len(iters)
     f = None
     out_taus, logs = [], []
     k = 0
+    v_eig = None
     for lev in range(n_levels):
         factor = 2 ** (n_levels - 1 - lev)
         gl = g.coarse(factor) if factor > 1 else g
@@ -367,7 +381,14 @@ def reconstruct(g: Geometry, y, lam: float, iters: Sequence[int], p: TVParams,
             f = np.zeros(gl.vol_shape) if f_init is None else _f64(f_init).copy()
         else:
             f = prolong(f)
-        tau = taus[lev] if taus is not None and taus[lev] > 0 else 1.0 / power_lipschitz(gl, power_iters)
+        if taus is not None and taus[lev] > 0:
+            tau = taus[lev]
+        else:
+            if lev > 0 and power_iters_fine > 0 and v_eig is not None:
+                L, v_eig = power_lipschitz_from(gl, prolong(v_eig), power_iters_fine)
+            else:
+                L, v_eig = power_lipschitz_from(gl, np.ones(gl.vol_shape), power_iters)
+            tau = 1.0 / L
         out_taus.append(tau)
         for _ in range(iters[lev]):
             rep = replay[k] if replay is not None else None

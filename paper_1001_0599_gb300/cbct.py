@@ -60,7 +60,8 @@ class TvStats(ctypes.Structure):
 class ReconParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("n_levels", ctypes.c_int),
                 ("iters", ctypes.c_int * CBCT_MAX_LEVELS), ("tau", ctypes.c_double * CBCT_MAX_LEVELS),
-                ("power_iters", ctypes.c_int), ("clamp", ctypes.c_int), ("tv", TvParams),
+                ("power_iters", ctypes.c_int), ("clamp", ctypes.c_int), ("power_iters_fine", ctypes.c_int),
+                ("tv", TvParams),
                 ("replay", ctypes.POINTER(ctypes.c_int32)), ("replay_len", ctypes.c_int)]
 
 
@@ -284,7 +285,8 @@ def cbct_power_lipschitz(geom: Geometry, level: int, n_iter: int, out, ws, strea
 
 def make_recon_params(lam: float, iters: Sequence[int], tv: Optional[TvParams] = None,
                       taus: Optional[Sequence[float]] = None, power_iters: int = 20, clamp: bool = True,
-                      replay: Optional[Sequence[Sequence[int]]] = None) -> ReconParams:
+                      replay: Optional[Sequence[Sequence[int]]] = None,
+                      power_iters_fine: int = 0) -> ReconParams:
     """ReconParams; ``replay`` is a list of per-iteration step-reduction lists."""
     p = ReconParams()
     p.lambda_ = lam
@@ -294,6 +296,7 @@ def make_recon_params(lam: float, iters: Sequence[int], tv: Optional[TvParams] =
         p.tau[i] = float(taus[i]) if taus is not None else 0.0
     p.power_iters = power_iters
     p.clamp = 1 if clamp else 0
+    p.power_iters_fine = power_iters_fine
     p.tv = tv if tv is not None else TvParams.paper()
     if replay is not None:
         flat = []

@@ -362,7 +362,7 @@ static double kappa_of(const VolGeom &v, const DetGeom &d) { return 2.0 * (doubl
 // workspace
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t state, partials, r, g, d, split, coarse[CBCT_MAX_LEVELS], replay, stats, hsino, hvol, total;
+    size_t state, partials, r, g, d, split, eig, coarse[CBCT_MAX_LEVELS], replay, stats, hsino, hvol, total;
     int n_partials;
 };
 
@@ -391,6 +391,9 @@ static Layout layout(const cbct_geometry *G, const cbct_recon_params *p, bool ho
     for (int l = 0; l < G->n_levels; l++) split = std::max(split, bp_split_floats(G->lev[l].vg, G->det));
     L.split = off;
     off = align_up(off + sizeof(float) * split);
+    // last power iterate of a coarse level, kept for the next level's warm start
+    L.eig = off;
+    if (G->n_levels > 1) off = align_up(off + sizeof(float) * nvox(G->lev[1].vg));
     const int levels = p ? std::max(1, std::min(p->n_levels, CBCT_MAX_LEVELS)) : 1;
     for (int l = 1; l < levels && l < G->n_levels; l++) {
         L.coarse[l] = off;
@@ -640,9 +643,11 @@ extern "C" cbct_status cbct_prolongate(int ncx, int ncy, int ncz, const float *d
     return ok();
 }
 
-// power iteration on level `level`; w and s live in the workspace (g and r)
+// power iteration on level `level`; w and s live in the workspace (g and r).
+// warm: start from the prolongation of the previous (coarser) level's last
+// iterate held in the eig buffer instead of from ones.
 static cbct_status run_power(const cbct_geometry *G, int level, int n_iter, void *ws, const Layout &L,
-                             double *d_L_out, cudaStream_t s)
+                             double *d_L_out, cudaStream_t s, bool warm = false)
 {
     const VolGeom &v = G->lev[level].vg;
     DevState *st = at<DevState>(ws, L.state);
@@ -650,8 +655,15 @@ static cbct_status run_power(const cbct_geometry *G, int level, int n_iter, void
     float *sino = at<float>(ws, L.r);
     double *partials = at<double>(ws, L.partials);
     const double kappa = kappa_of(v, G->det);
-    CUDA_TRY(launch_power_init(st, (double)nvox(v), s));
-    CUDA_TRY(launch_fill(w, nvox(v), 1.f, s));
+    if (warm) {
+        const VolGeom &vc = G->lev[level + 1].vg;
+        CUDA_TRY(launch_prolong(vc.nx, vc.ny, vc.nz, at<float>(ws, L.eig), w, s));
+        CUDA_TRY(launch_sumsq(w, nvox(v), partials, 1024, &st->vnorm2, s));
+        CUDA_TRY(launch_power_init(st, 0.0, s));
+    } else {
+        CUDA_TRY(launch_power_init(st, (double)nvox(v), s));
+        CUDA_TRY(launch_fill(w, nvox(v), 1.f, s));
+    }
     for (int it = 0; it < n_iter; it++) {
         // projection pre-weighted by ds (mode 3) feeds the transpose's staged patch directly
         CUDA_TRY(launch_forward(v, G->det, w, nullptr, sino, &st->inv_wnorm, nullptr, 3, s));
@@ -699,6 +711,8 @@ static cbct_status check_recon_params(const cbct_geometry *G, const cbct_recon_p
     }
     if (total > CBCT_MAX_ITERS) return fail(CBCT_ERR_INVALID_ARG, "more than %d iterations", CBCT_MAX_ITERS);
     if (p->power_iters < 0 || p->power_iters > 10000) return fail(CBCT_ERR_INVALID_ARG, "power_iters out of range");
+    if (p->power_iters_fine < 0 || p->power_iters_fine > 10000)
+        return fail(CBCT_ERR_INVALID_ARG, "power_iters_fine out of range");
     CHECK(check_tv_params(&p->tv));
     replay_off.clear();
     if (p->replay) {
@@ -739,6 +753,7 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
     const int power_iters = p->power_iters > 0 ? p->power_iters : 20;
     float *prev = nullptr;
     int k = 0;
+    int eig_level = -1;   // geometry level whose last power iterate sits in the eig buffer
     for (int lev = 0; lev < Lv; lev++) {
         const int gl = Lv - 1 - lev;  // geometry level: 0 = finest
         const VolGeom &v = G->lev[gl].vg;
@@ -750,7 +765,15 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
             CUDA_TRY(launch_prolong(vc.nx, vc.ny, vc.nz, prev, f, s));
         }
         const double kappa = kappa_of(v, G->det);
-        if (!(p->tau[lev] > 0)) CHECK(run_power(G, gl, power_iters, ws, L, nullptr, s));
+        if (!(p->tau[lev] > 0)) {
+            const bool warm = p->power_iters_fine > 0 && eig_level == gl + 1;
+            CHECK(run_power(G, gl, warm ? p->power_iters_fine : power_iters, ws, L, nullptr, s, warm));
+            if (p->power_iters_fine > 0 && gl > 0) {
+                CUDA_TRY(cudaMemcpyAsync(at<float>(ws, L.eig), at<float>(ws, L.g), sizeof(float) * nvox(v),
+                                         cudaMemcpyDeviceToDevice, s));
+                eig_level = gl;
+            }
+        }
         CUDA_TRY(launch_set_tau(st, p->tau[lev] > 0 ? p->tau[lev] : 0.0, kappa, d_stats, lev, s));
         const double inv_m = 1.0 / (double)nray(G->det);
         for (int it = 0; it < p->iters[lev]; it++, k++) {

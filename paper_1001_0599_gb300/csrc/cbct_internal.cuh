@@ -217,7 +217,8 @@ cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, c
 cudaError_t launch_sum_partials(const double *partials, int n, int stride, int k, double *out,
                                 cudaStream_t s);
 cudaError_t launch_e2(const double *partials, int n, double inv_m, DevState *st, cudaStream_t s);
-cudaError_t launch_power_init(DevState *st, double nvox, cudaStream_t s);
+cudaError_t launch_power_init(DevState *st, double nvox, cudaStream_t s);   // nvox <= 0: keep vnorm2
+cudaError_t launch_sumsq(const float *x, size_t n, double *partials, int blocks, double *out, cudaStream_t s);
 cudaError_t launch_power_update(DevState *st, const double *partials, int n, double kappa_unused,
                                 int first, int last, double *d_L_out, cudaStream_t s);
 cudaError_t launch_set_tau(DevState *st, double tau_given, double kappa, cbct_recon_stats *rs,

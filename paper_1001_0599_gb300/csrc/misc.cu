@@ -97,9 +97,43 @@ cudaError_t launch_power_update(DevState *st, const double *partials, int n, dou
 __global__ void power_init_kernel(DevState *st, double nvox)
 {
     if (threadIdx.x == 0) {
-        st->vnorm2 = nvox;
+        if (nvox > 0.0) st->vnorm2 = nvox;   // start from ones; otherwise vnorm2 was set by a norm pass
         st->inv_wnorm = 1.0;
     }
+}
+
+// per-block sums of x^2 (compensated FP32 in the block, FP64 out)
+__global__ void __launch_bounds__(256) sumsq_kernel(const float *__restrict__ x, size_t n,
+                                                    double *__restrict__ partials)
+{
+    __shared__ double red[32];
+    float acc = 0.f;
+    DF v[1] = {df_zero()};
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    int k = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float t = __ldg(x + i);
+        acc += t * t;
+        if (++k == 16) {
+            v[0] = df_add(v[0], acc);
+            acc = 0.f;
+            k = 0;
+        }
+    }
+    v[0] = df_add(v[0], acc);
+    double tot[1];
+    block_sum_df<1>(v, red, tot);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot[0];
+}
+
+cudaError_t launch_sumsq(const float *x, size_t n, double *partials, int blocks, double *out, cudaStream_t s)
+{
+    launch_begin(K_REDUCE, s);
+    sumsq_kernel<<<blocks, 256, 0, s>>>(x, n, partials);
+    note_extra_launch();
+    sum_partials_kernel<<<1, 1024, 0, s>>>(partials, blocks, 1, 1, out, 1.0);
+    launch_end(K_REDUCE, s);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_power_init(DevState *st, double nvox, cudaStream_t s)

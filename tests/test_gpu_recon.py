@@ -30,11 +30,11 @@ def _tv(lib, p):
     return lib.TvParams(p.eps_tv, p.c, p.alpha, p.rel_tol, p.max_inner, p.max_backtracks, p.s0)
 
 
-def _run(lib, wl, y, iters, p, lam, taus=None, replay=None, power_iters=20):
+def _run(lib, wl, y, iters, p, lam, taus=None, replay=None, power_iters=20, power_iters_fine=0):
     import torch
     g = lib.geometry_from_workload(wl)
     params = lib.make_recon_params(lam, iters, _tv(lib, p), taus=taus, power_iters=power_iters,
-                                   replay=replay)
+                                   replay=replay, power_iters_fine=power_iters_fine)
     ws = lib.workspace(lib.cbct_workspace_size(g, params))
     st = lib.stats_buffer()
     vol = torch.zeros(g.vol_shape, device="cuda")
@@ -94,6 +94,19 @@ def test_multigrid_recon_replay_parity(lib, orc):
     for lev in range(3):
         assert st.tau[lev] == pytest.approx(ref.taus[lev], rel=1e-5)
     assert [st.iters[k].level for k in range(10)] == [0] * 4 + [1] * 3 + [2] * 3
+    assert rel_l2(got, ref.f) < TOL_RECON
+
+
+def test_multigrid_warm_started_step_sizes(lib, orc):
+    from paper_1001_0599_gb300 import synthetic
+    wl = synthetic.Workload("mgw", 32, 32, 16, 4.0, 4.0, 4.0, 64, 48, 1.6, 1.6, 12, photons=5e4,
+                            phantom="head_neck", phantom_seed=3, noise_seed=4, lam=0.05, iters=(3, 2, 2))
+    og, truth, y = _problem(wl, orc)
+    p = orc.TVParams(eps_tv=1e-5)
+    ref = orc.reconstruct(og, y, wl.lam, wl.iters, p, power_iters_fine=3)
+    got, st = _run(lib, wl, y, wl.iters, p, wl.lam, replay=ref.schedule(), power_iters_fine=3)
+    for lev in range(3):
+        assert st.tau[lev] == pytest.approx(ref.taus[lev], rel=1e-5)
     assert rel_l2(got, ref.f) < TOL_RECON
 
 

@@ -138,3 +138,20 @@ def test_reconstruct_multigrid_schedule_and_quality_trend(orc):
         assert res.iters[0].level == 0 and res.iters[-1].level == 1
         errs.append(np.linalg.norm(res.f - truth) / np.linalg.norm(truth))
     assert errs[1] < errs[0]
+
+
+def test_warm_started_power_iteration_converges_to_eigvalsh(orc):
+    # start vector: prolongation of the coarse grid's dominant eigenvector
+    g = orc.Geometry(6, 6, 4, 2.0, 2.0, 2.0, 12, 8, 2.0, 2.0, 200.0, 320.0,
+                     np.linspace(0, 2 * np.pi, 5, endpoint=False), 0.5)
+    gc = g.coarse(2)
+    A = dense(orc, g)
+    lam_max = np.linalg.eigvalsh(orc.kappa(g) * A.T @ A)[-1]
+    _, vc = orc.power_lipschitz_from(gc, np.ones(gc.vol_shape), 50)
+    L_warm, v = orc.power_lipschitz_from(g, orc.prolong(vc), 40)
+    assert L_warm == pytest.approx(lam_max, rel=1e-10)
+    assert np.linalg.norm(v) == pytest.approx(1.0, rel=1e-12)
+    # from ones the same start behaves like the plain routine
+    L_cold, _ = orc.power_lipschitz_from(g, np.ones(g.vol_shape), 25)
+    assert L_cold == pytest.approx(orc.power_lipschitz(g, 25), rel=1e-14)
+    assert L_cold <= lam_max * (1 + 1e-12)
