@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--power-fine", type=int, default=4,
                     help="power iterations on each level after the first, warm-started from the "
                          "prolongated eigenvector of the previous level (0: 20 from ones everywhere)")
+    ap.add_argument("--gradient", default="matched", choices=["matched", "eq6"],
+                    help="Step 1 gradient: matched transpose P^T or the paper's closed form (Eq. 6)")
     ap.add_argument("--level", type=int, default=0,
                     help="one-iteration mode: multigrid level (0 = finest)")
     ap.add_argument("--mode", default="recon", choices=["recon", "one-iteration"],
@@ -248,7 +250,7 @@ def main():
         params = cbct.make_recon_params(wl.lam, iters, tv, taus=[1.28e-5] * (args.level + 1), clamp=True)
     else:
         params = cbct.make_recon_params(wl.lam, wl.iters, tv, power_iters=20, clamp=True,
-                                        power_iters_fine=args.power_fine)
+                                        power_iters_fine=args.power_fine, gradient=args.gradient)
     ws = cbct.workspace(cbct.cbct_workspace_size(g, params))
     stats = cbct.stats_buffer()
     d_y = torch.from_numpy(y.astype(np.float32)).cuda()
@@ -350,6 +352,8 @@ def main():
         "tau = 1/L (20 power iterations per level)",
         f"tau = 1/L (20 power iterations on the coarsest level, {args.power_fine} per finer level "
         f"warm-started from the prolongated eigenvector)")
+    if args.gradient == "eq6":
+        workload += "; Step 1 gradient from the paper's closed form (Eq. 6) instead of the matched transpose"
     line = {"metric": METRIC, "value": sec_per_scan, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -98,6 +98,8 @@ typedef struct {
     int power_iters_fine;            /* > 0: every level after the first runs this many power
                                         iterations started from the prolongation of the previous
                                         level's last iterate instead of power_iters from ones */
+    int gradient_mode;               /* Step 1 gradient: 0 = matched P^T (exact gradient of E2),
+                                        1 = the paper's closed form, Eq. 6 (unmatched, cheaper) */
     cbct_tv_params tv;
     /* Optional replay of a recorded step schedule (testing): host array of
      * records, one per FBS iteration in order: n, then n step-reduction
@@ -178,6 +180,13 @@ cbct_status cbct_residual_static(const cbct_geometry *geom, const float *d_vol, 
  * voxel written once. Overwrites d_vol. */
 cbct_status cbct_back_project(const cbct_geometry *geom, const float *d_sino, float *d_vol,
                               void *stream);
+
+/* The paper's closed-form gradient of the data term (Eq. 6 with Eq. A6, A7),
+ * voxel-driven: d_vol(x) = sum over views of 2 L^3(u*,v*) / (L0 l^2(x)) *
+ * T(u*, v*), T = d_T bilinearly interpolated on the detector (zero outside),
+ * without Eq. 6's 1/(N_theta A) prefactor. Not the transpose of P: it tends
+ * to 2 du dv / (voxel volume) * P^T T as the grids refine. Overwrites d_vol. */
+cbct_status cbct_eq6_gradient(const cbct_geometry *geom, const float *d_T, float *d_vol, void *stream);
 
 /* Step 1 of Algorithm A1: d_g = d_f - scale * P^T d_r, with scale = tau*kappa,
  * kappa = 2 N_vox / (N_theta N_pix) for the mean-normalised E2 of Eq. 2.

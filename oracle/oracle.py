@@ -322,6 +322,20 @@ class IterLog:
     steps: List[int]
 
 
+def fbs_iteration_eq6(g: Geometry, y, f, lam: float, tau: float, p: TVParams, clamp: bool = True,
+                      replay: Optional[Sequence[int]] = None):
+    """Algorithm A1 iteration with Step 1 taken from Eq. 6 instead of P^T:
+    g = f - tau kappa (voxel volume / (2 du dv)) G(P f - y). In place on f."""
+    r = forward_project(g, f) - _f64(y)
+    e2 = float(np.mean(r * r))
+    factor = g.dx * g.dy * g.dz / (2.0 * g.du * g.dv)
+    gaux = f - tau * kappa(g) * factor * eq6_backproject(g, r)
+    res = rof_solve(g, gaux, lam, tau, p, replay=replay)
+    f[...] = np.maximum(res.f, 0.0) if clamp else res.f
+    st = _RofStats(res.n_inner, res.flags, res.e_first, res.e_last)
+    return e2, st, res.log
+
+
 def fbs_iteration(g: Geometry, y, f, lam: float, tau: float, p: TVParams, clamp: bool = True,
                   replay: Optional[Sequence[int]] = None):
     """One Algorithm A1 iteration in place on ``f``; returns (e2, RofStats, log)."""
@@ -355,7 +369,7 @@ def reconstruct(g: Geometry, y, lam: float, iters: Sequence[int], p: TVParams,
                 taus: Optional[Sequence[float]] = None, power_iters: int = 20,
                 clamp: bool = True, f_init=None,
                 replay: Optional[Sequence[Sequence[int]]] = None,
-                power_iters_fine: int = 0) -> ReconResult:
+                power_iters_fine: int = 0, gradient: str = "matched") -> ReconResult:
     """Algorithm A1 under the coarse-to-fine schedule of Sec. II.C.3.
 
     ``iters`` lists the FBS iterations per level, coarsest first; level l of
@@ -392,7 +406,8 @@ def reconstruct(g: Geometry, y, lam: float, iters: Sequence[int], p: TVParams,
         out_taus.append(tau)
         for _ in range(iters[lev]):
             rep = replay[k] if replay is not None else None
-            e2, st, steps = fbs_iteration(gl, y, f, lam, tau, p, clamp, rep)
+            step = fbs_iteration_eq6 if gradient == "eq6" else fbs_iteration
+            e2, st, steps = step(gl, y, f, lam, tau, p, clamp, rep)
             logs.append(IterLog(lev, e2, st.n_inner, st.flags, st.e_first, st.e_last,
                                 [int(s) for s in steps]))
             k += 1

@@ -61,7 +61,7 @@ class ReconParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("n_levels", ctypes.c_int),
                 ("iters", ctypes.c_int * CBCT_MAX_LEVELS), ("tau", ctypes.c_double * CBCT_MAX_LEVELS),
                 ("power_iters", ctypes.c_int), ("clamp", ctypes.c_int), ("power_iters_fine", ctypes.c_int),
-                ("tv", TvParams),
+                ("gradient_mode", ctypes.c_int), ("tv", TvParams),
                 ("replay", ctypes.POINTER(ctypes.c_int32)), ("replay_len", ctypes.c_int)]
 
 
@@ -105,6 +105,8 @@ def load() -> ctypes.CDLL:
     L.cbct_residual_static.restype = st
     L.cbct_back_project.argtypes = [_P, _P, _P, _P]
     L.cbct_back_project.restype = st
+    L.cbct_eq6_gradient.argtypes = [_P, _P, _P, _P]
+    L.cbct_eq6_gradient.restype = st
     L.cbct_gradient_step.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
     L.cbct_gradient_step.restype = st
     d = ctypes.c_double
@@ -249,6 +251,10 @@ def cbct_back_project(geom: Geometry, sino, vol, stream=None) -> None:
     _check(load().cbct_back_project(geom.handle, _f32(sino, "sino"), _f32(vol, "vol"), _stream(stream)))
 
 
+def cbct_eq6_gradient(geom: Geometry, T, vol, stream=None) -> None:
+    _check(load().cbct_eq6_gradient(geom.handle, _f32(T, "T"), _f32(vol, "vol"), _stream(stream)))
+
+
 def cbct_gradient_step(geom: Geometry, r, f, g, scale: float, stream=None) -> None:
     _check(load().cbct_gradient_step(geom.handle, _f32(r, "r"), _f32(f, "f"), _f32(g, "g"), float(scale),
                                      _stream(stream)))
@@ -286,7 +292,7 @@ def cbct_power_lipschitz(geom: Geometry, level: int, n_iter: int, out, ws, strea
 def make_recon_params(lam: float, iters: Sequence[int], tv: Optional[TvParams] = None,
                       taus: Optional[Sequence[float]] = None, power_iters: int = 20, clamp: bool = True,
                       replay: Optional[Sequence[Sequence[int]]] = None,
-                      power_iters_fine: int = 0) -> ReconParams:
+                      power_iters_fine: int = 0, gradient: str = "matched") -> ReconParams:
     """ReconParams; ``replay`` is a list of per-iteration step-reduction lists."""
     p = ReconParams()
     p.lambda_ = lam
@@ -297,6 +303,7 @@ def make_recon_params(lam: float, iters: Sequence[int], tv: Optional[TvParams] =
     p.power_iters = power_iters
     p.clamp = 1 if clamp else 0
     p.power_iters_fine = power_iters_fine
+    p.gradient_mode = {"matched": 0, "eq6": 1}[gradient]
     p.tv = tv if tv is not None else TvParams.paper()
     if replay is not None:
         flat = []

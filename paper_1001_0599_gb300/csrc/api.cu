@@ -62,7 +62,7 @@ int64_t g_prof_count[K_COUNT] = {};
 double g_prof_ms[K_COUNT] = {};
 const char *g_names[K_COUNT] = {"forward_project", "forward_residual", "back_project",
                                 "back_project_step", "rof_persistent", "reduce",
-                                "prolongate", "fill", "misc"};
+                                "prolongate", "fill", "misc", "eq6_gradient"};
 } // namespace
 
 namespace cbct {
@@ -486,6 +486,15 @@ extern "C" cbct_status cbct_back_project(const cbct_geometry *G, const float *d_
     return ok();
 }
 
+extern "C" cbct_status cbct_eq6_gradient(const cbct_geometry *G, const float *d_T, float *d_vol, void *stream)
+{
+    CHECK(check_geom(G));
+    CHECK(check_ptr(d_T, "d_T"));
+    CHECK(check_ptr(d_vol, "d_vol"));
+    CUDA_TRY(launch_eq6(G->lev[0].vg, G->det, d_T, nullptr, d_vol, nullptr, 0.0, 0, (cudaStream_t)stream));
+    return ok();
+}
+
 extern "C" cbct_status cbct_gradient_step(const cbct_geometry *G, const float *d_r, const float *d_f, float *d_g,
                                           double scale, void *stream)
 {
@@ -713,6 +722,8 @@ static cbct_status check_recon_params(const cbct_geometry *G, const cbct_recon_p
     if (p->power_iters < 0 || p->power_iters > 10000) return fail(CBCT_ERR_INVALID_ARG, "power_iters out of range");
     if (p->power_iters_fine < 0 || p->power_iters_fine > 10000)
         return fail(CBCT_ERR_INVALID_ARG, "power_iters_fine out of range");
+    if (p->gradient_mode != 0 && p->gradient_mode != 1)
+        return fail(CBCT_ERR_INVALID_ARG, "gradient_mode must be 0 (matched P^T) or 1 (Eq. 6)");
     CHECK(check_tv_params(&p->tv));
     replay_off.clear();
     if (p->replay) {
@@ -777,10 +788,20 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
         CUDA_TRY(launch_set_tau(st, p->tau[lev] > 0 ? p->tau[lev] : 0.0, kappa, d_stats, lev, s));
         const double inv_m = 1.0 / (double)nray(G->det);
         for (int it = 0; it < p->iters[lev]; it++, k++) {
-            // Step 1: r = ds (P f - y), E2; g = f - tau kappa P^T r
-            CUDA_TRY(launch_forward(v, G->det, f, d_sino, r, nullptr, partials, 2, s));
-            CUDA_TRY(launch_e2(partials, fp_partials_count(v, G->det), inv_m, st, s));
-            CUDA_TRY(launch_back(v, G->det, r, f, g, &st->scale, 0.0, 0.0, nullptr, 1, 1, at<float>(ws, L.split), s));
+            if (p->gradient_mode == 1) {
+                // Step 1 with the paper's closed-form gradient (Eq. 6) in place of P^T:
+                // P^T T tends to (voxel volume / (2 du dv)) G(T) (Eq. 6 carries a factor 2)
+                CUDA_TRY(launch_forward(v, G->det, f, d_sino, r, nullptr, partials, 1, s));
+                CUDA_TRY(launch_e2(partials, fp_partials_count(v, G->det), inv_m, st, s));
+                const double eq6_factor = (double)v.dx * v.dy * v.dz / (2.0 * (double)G->det.du * G->det.dv);
+                CUDA_TRY(launch_eq6(v, G->det, r, f, g, &st->scale, eq6_factor, 1, s));
+            } else {
+                // Step 1: r = ds (P f - y), E2; g = f - tau kappa P^T r
+                CUDA_TRY(launch_forward(v, G->det, f, d_sino, r, nullptr, partials, 2, s));
+                CUDA_TRY(launch_e2(partials, fp_partials_count(v, G->det), inv_m, st, s));
+                CUDA_TRY(launch_back(v, G->det, r, f, g, &st->scale, 0.0, 0.0, nullptr, 1, 1, at<float>(ws, L.split),
+                                     s));
+            }
             // Steps 2-3: ROF from g, clamp fused into its last update
             RofArgs a = rof_base(G, gl, ws, L);
             a.g = g;

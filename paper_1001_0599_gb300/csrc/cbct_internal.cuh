@@ -174,6 +174,7 @@ enum KernelId {
     K_PROLONG,
     K_FILL,
     K_MISC,
+    K_EQ6,
     K_COUNT
 };
 
@@ -212,6 +213,11 @@ size_t bp_smem_bound(const VolGeom &v, const DetGeom &d);
 cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, const float *f,
                         float *out, const double *d_scale, double scale_val, double kappa,
                         double *partials, int mode, int prescaled, float *split_ws, cudaStream_t s);
+
+// Eq. 6 voxel-driven gradient (eq6.cu). mode 0: out = G(T); mode 1:
+// out = f - scale G(T) with scale = scale_val (* *d_scale when given)
+cudaError_t launch_eq6(const VolGeom &v, const DetGeom &d, const float *T, const float *f, float *out,
+                       const double *d_scale, double scale_val, int mode, cudaStream_t s);
 
 // small kernels (misc.cu)
 cudaError_t launch_sum_partials(const double *partials, int n, int stride, int k, double *out,

@@ -176,3 +176,41 @@ def test_paper_scale_sampled_parity(lib, orc):
         ref.append(float(np.dot(w, s[vv, ii, uu])))
         got.append(bth.ravel()[j])
     assert rel_l2(got, ref) < TOL_CALL
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_eq6_gradient_matches_oracle(lib, orc, case):
+    import torch
+    wl, g, og = geometries(case)
+    T = f32(np.random.default_rng(8).standard_normal(og.sino_shape))
+    out = torch.full(og.vol_shape, float("nan"), device="cuda")
+    lib.cbct_eq6_gradient(g, dev(T), out)
+    ref = orc.eq6_backproject(og, T)
+    got = host(out)
+    assert np.all(np.isfinite(got))
+    # Eq. 6 interpolates the detector at a coordinate computed in FP32: its
+    # index coordinate (up to max(nu, nv)) carries an absolute rounding error
+    # of about one ulp, i.e. 2^-23 max(nu, nv) pixels, which on a white-noise
+    # sinogram shifts the result by about that fraction of its norm
+    tol = max(TOL_CALL, 2.0 ** -23 * max(og.nu, og.nv))
+    assert rel_l2(got, ref) < tol
+
+
+def test_eq6_tends_to_matched_transpose(lib):
+    # on a smooth detector function Eq. 6 approaches the matched transpose
+    # scaled by voxel volume / (2 du dv) (the continuum limit of P^T)
+    import torch
+    from paper_1001_0599_gb300 import synthetic
+    wl = synthetic.Workload("fine", 48, 48, 32, 0.5, 0.5, 0.5, 160, 120, 0.4, 0.4, 6, sad=600.0, sdd=900.0)
+    g = lib.geometry_from_workload(wl)
+    uu = (np.arange(wl.nu) - 0.5 * (wl.nu - 1)) * wl.du
+    vv = (np.arange(wl.nv) - 0.5 * (wl.nv - 1)) * wl.dv
+    T = np.broadcast_to(1.0 + 0.3 * np.cos(uu[None, None, :] / 9.0) * np.exp(-(vv[None, :, None] / 30.0) ** 2),
+                        (wl.n_views, wl.nv, wl.nu))
+    a = torch.empty(g.vol_shape, device="cuda")
+    b = torch.empty(g.vol_shape, device="cuda")
+    lib.cbct_back_project(g, dev(T), a)
+    lib.cbct_eq6_gradient(g, dev(T), b)
+    scale = wl.dx * wl.dy * wl.dz / (2 * wl.du * wl.dv)
+    inner = (slice(6, -6), slice(6, -6), slice(4, -4))
+    assert rel_l2(scale * host(b)[inner], host(a)[inner]) < 0.02

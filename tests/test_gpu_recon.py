@@ -30,11 +30,12 @@ def _tv(lib, p):
     return lib.TvParams(p.eps_tv, p.c, p.alpha, p.rel_tol, p.max_inner, p.max_backtracks, p.s0)
 
 
-def _run(lib, wl, y, iters, p, lam, taus=None, replay=None, power_iters=20, power_iters_fine=0):
+def _run(lib, wl, y, iters, p, lam, taus=None, replay=None, power_iters=20, power_iters_fine=0,
+         gradient="matched"):
     import torch
     g = lib.geometry_from_workload(wl)
     params = lib.make_recon_params(lam, iters, _tv(lib, p), taus=taus, power_iters=power_iters,
-                                   replay=replay, power_iters_fine=power_iters_fine)
+                                   replay=replay, power_iters_fine=power_iters_fine, gradient=gradient)
     ws = lib.workspace(lib.cbct_workspace_size(g, params))
     st = lib.stats_buffer()
     vol = torch.zeros(g.vol_shape, device="cuda")
@@ -108,6 +109,17 @@ def test_multigrid_warm_started_step_sizes(lib, orc):
     for lev in range(3):
         assert st.tau[lev] == pytest.approx(ref.taus[lev], rel=1e-5)
     assert rel_l2(got, ref.f) < TOL_RECON
+
+
+def test_eq6_gradient_recon_replay_parity(lib, orc, small):
+    # Algorithm A1 with the paper's closed-form Step 1 (Eq. 6) instead of P^T
+    wl, og, truth, y, p, tau, ref = small
+    ref6 = orc.reconstruct(og, y, wl.lam, (4,), p, taus=[tau], gradient="eq6")
+    got, st = _run(lib, wl, y, (4,), p, wl.lam, taus=[tau], replay=ref6.schedule(), gradient="eq6")
+    assert st.status == 0
+    assert rel_l2(got, ref6.f) < TOL_RECON
+    for k, it in enumerate(ref6.iters):
+        assert st.iters[k].e2 == pytest.approx(it.e2, rel=1e-5)
 
 
 def test_recon_without_clamp_and_nonneg_with(lib, orc, small):
