@@ -8,8 +8,9 @@
  * cudaStream_t; NULL = the legacy default stream) and returns after argument
  * checks; argument errors are reported synchronously and nothing is launched.
  * The library never allocates device memory inside a compute call: device
- * memory is allocated only by cbct_geometry_create (its ray tables), and
- * every other buffer is caller-owned. No C++ exception crosses this boundary.
+ * memory is allocated only by cbct_geometry_create (its ray tables) and by
+ * cbct_server_create (the serving arena), and every other buffer is
+ * caller-owned. No C++ exception crosses this boundary.
  *
  * Layouts (caller-owned device arrays, 16-byte aligned, contiguous, FP32):
  *   volume   f[a][b][c], a < nx, b < ny, c < nz (z fastest). Voxel centres
@@ -256,6 +257,66 @@ cbct_status cbct_workspace_size_host(const cbct_geometry *geom, const cbct_recon
 cbct_status cbct_reconstruct_host(const cbct_geometry *geom, const float *h_sino, float *h_vol,
                                   const cbct_recon_params *params, void *d_ws, size_t ws_bytes,
                                   cbct_recon_stats *h_stats, void *stream);
+
+/* ---- serving: a native scheduler for streams of scans -------------------
+ *
+ * The paper reconstructs one scan at a time; this runtime (no counterpart in
+ * the paper) serves a stream of independent scans on one GPU. It owns one
+ * device arena, allocated once at creation, from which each admitted scan
+ * receives a resident slot (sinogram, volume, workspace, statistics). A scan
+ * is admitted, in arrival order, when its slot fits in the arena (an idle
+ * slot of the same geometry and parameters is reused; idle slots of other
+ * shapes are evicted, least recently used first, to make room). Admitted
+ * scans are copied in on a host-to-device stream, reconstructed one at a time
+ * on a compute stream (the TV step is a grid-wide cooperative kernel that
+ * fills the GPU, so reconstructions are serialised), and copied out on a
+ * device-to-host stream, so copies overlap computation. With use_graphs, the
+ * first reconstruction in a slot is captured as a CUDA graph and every later
+ * scan in that slot replays it (one launch per scan).
+ *
+ * Host buffers must be page-locked (cudaHostAlloc / cudaHostRegister) and stay
+ * valid, like the geometry, until the scan's cbct_server_wait returns. Slots
+ * are matched to geometries by a serial number given at creation, so a slot
+ * is never reused for a new geometry that happens to share an address. All
+ * entry points are thread-safe. While a server exists its worker threads
+ * launch kernels; kernel profiling (cbct_profile_*) does not see them. */
+typedef struct cbct_server cbct_server;
+
+typedef struct {
+    size_t arena_bytes;   /* device bytes for resident scans; 0: half the free memory, at most 64 GiB */
+    int max_resident;     /* resident slots at most (0: no limit) */
+    int use_graphs;       /* 1: capture each slot's reconstruction once and replay it */
+} cbct_server_config;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t status;         /* cbct_status of the scan */
+    int32_t graph_replay;   /* 1: ran as a replay of the slot's captured graph */
+    uint32_t recon_flags;   /* cbct_recon_stats.flags */
+    int32_t slot;           /* slot index it ran in */
+    double t_submit, t_admit, t_done;  /* host seconds since server creation */
+    double gpu_ms;          /* device time of the reconstruction (CUDA events) */
+} cbct_scan_result;
+
+typedef struct {
+    size_t arena_bytes, bytes_in_use, peak_bytes_in_use;
+    int32_t slots, busy_slots, graphs_captured, graph_failures;
+    int64_t submitted, completed, evictions;
+} cbct_server_info;
+
+cbct_status cbct_server_create(const cbct_server_config *cfg, cbct_server **out);
+/* Waits for every submitted scan, then frees the arena, graphs and threads. */
+void cbct_server_destroy(cbct_server *server);
+/* Queue one scan: reconstruct h_sino (page-locked, n_views*nv*nu floats)
+ * with params (no replay schedule) into h_vol (page-locked, nx*ny*nz floats);
+ * h_stats (page-locked, optional). Rejects a scan whose slot cannot fit in
+ * the arena even when it is empty (CBCT_ERR_OUT_OF_MEMORY). */
+cbct_status cbct_server_submit(cbct_server *server, const cbct_geometry *geom, const cbct_recon_params *params,
+                               const float *h_sino, float *h_vol, cbct_recon_stats *h_stats, uint64_t *ticket);
+/* Block until the scan is done and its result is in h_vol; fills *result.
+ * Each ticket can be waited for once. */
+cbct_status cbct_server_wait(cbct_server *server, uint64_t ticket, cbct_scan_result *result);
+cbct_status cbct_server_query(cbct_server *server, cbct_server_info *info);
 
 /* ---- diagnostics -------------------------------------------------------- */
 

@@ -21,7 +21,8 @@ LIB = os.path.join(HERE, "libcbct.so")
 # split over six objects so they compile in parallel
 SOURCES = [("api.cu", "api.o", ()), ("fp.cu", "fp.o", ())] + \
     [("bp.cu", f"bp{u}.o", (f"-DBP_MODE_UNIT={u}",)) for u in range(6)] + \
-    [("tv.cu", "tv.o", ()), ("misc.cu", "misc.o", ()), ("noalloc.cu", "noalloc.o", ()), ("eq6.cu", "eq6.o", ())]
+    [("tv.cu", "tv.o", ()), ("misc.cu", "misc.o", ()), ("noalloc.cu", "noalloc.o", ()), ("eq6.cu", "eq6.o", ()),
+                                                                                     ("serve.cu", "serve.o", ())]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -74,7 +75,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC", "-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

@@ -78,6 +78,23 @@ class ReconStats(ctypes.Structure):
                 ("steps", ctypes.c_int32 * CBCT_MAX_STEP_LOG)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_resident", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+
+
+class ScanResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("graph_replay", ctypes.c_int32),
+                ("recon_flags", ctypes.c_uint32), ("slot", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("gpu_ms", ctypes.c_double)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes_in_use", ctypes.c_size_t), ("slots", ctypes.c_int32), ("busy_slots", ctypes.c_int32),
+                ("graphs_captured", ctypes.c_int32), ("graph_failures", ctypes.c_int32),
+                ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("evictions", ctypes.c_int64)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 
@@ -129,6 +146,16 @@ def load() -> ctypes.CDLL:
     L.cbct_reconstruct_host.argtypes = [_P, _P, _P, ctypes.POINTER(ReconParams), _P, ctypes.c_size_t,
                                         ctypes.POINTER(ReconStats), _P]
     L.cbct_reconstruct_host.restype = st
+    L.cbct_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]
+    L.cbct_server_create.restype = st
+    L.cbct_server_destroy.argtypes = [_P]
+    L.cbct_server_destroy.restype = None
+    L.cbct_server_submit.argtypes = [_P, _P, ctypes.POINTER(ReconParams), _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]
+    L.cbct_server_submit.restype = st
+    L.cbct_server_wait.argtypes = [_P, ctypes.c_uint64, ctypes.POINTER(ScanResult)]
+    L.cbct_server_wait.restype = st
+    L.cbct_server_query.argtypes = [_P, ctypes.POINTER(ServerInfo)]
+    L.cbct_server_query.restype = st
     L.cbct_last_error.argtypes = []
     L.cbct_last_error.restype = ctypes.c_char_p
     L.cbct_launch_count.argtypes = []
@@ -394,3 +421,80 @@ def cbct_profile_query() -> dict:
         _check(L.cbct_profile_query(k, ctypes.byref(n), ctypes.byref(ms)))
         out[L.cbct_profile_name(k).decode()] = (int(n.value), float(ms.value))
     return out
+
+
+# ---- serving ---------------------------------------------------------------
+
+def _host_ptr(t, name, dtype):
+    """Address of a contiguous, page-locked CPU tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != dtype:
+        raise TypeError(f"{name} must be a CPU {dtype} tensor")
+    if not t.is_contiguous() or not t.is_pinned():
+        raise ValueError(f"{name} must be contiguous and pinned (tensor.pin_memory())")
+    return t.data_ptr()
+
+
+class Server:
+    """Owning wrapper of a cbct_server: a native scheduler that admits scans
+    into resident slots of one device arena and reconstructs them in arrival
+    order, overlapping copies with computation (see include/cbct.h)."""
+
+    def __init__(self, arena_bytes: int = 0, max_resident: int = 0, use_graphs: bool = True):
+        L = load()
+        self.cfg = ServerConfig(int(arena_bytes), int(max_resident), 1 if use_graphs else 0)
+        h = _P()
+        _check(L.cbct_server_create(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, geom: Geometry, params: ReconParams, h_sino, h_vol, h_stats=None) -> int:
+        """Queue one scan; h_sino and h_vol are pinned float32 CPU tensors of the
+        geometry's sinogram and volume shapes; returns its ticket."""
+        import torch
+        if tuple(h_sino.shape) != tuple(geom.sino_shape) or tuple(h_vol.shape) != tuple(geom.vol_shape):
+            raise ValueError("h_sino / h_vol shapes do not match the geometry")
+        stats_ptr = None
+        if h_stats is not None:
+            if not isinstance(h_stats, torch.Tensor) or h_stats.numel() < ctypes.sizeof(ReconStats):
+                raise ValueError("h_stats must be a pinned uint8 tensor of sizeof(cbct_recon_stats) bytes")
+            stats_ptr = _host_ptr(h_stats, "h_stats", torch.uint8)
+        t = ctypes.c_uint64()
+        _check(load().cbct_server_submit(self.handle, geom.handle, ctypes.byref(params),
+                                         _host_ptr(h_sino, "h_sino", torch.float32),
+                                         _host_ptr(h_vol, "h_vol", torch.float32), stats_ptr, ctypes.byref(t)))
+        # the geometry, params and host buffers must outlive the scan
+        self._keep[t.value] = (geom, params, h_sino, h_vol, h_stats)
+        return t.value
+
+    def wait(self, ticket: int) -> ScanResult:
+        res = ScanResult()
+        st = load().cbct_server_wait(self.handle, ctypes.c_uint64(ticket), ctypes.byref(res))
+        self._keep.pop(ticket, None)
+        _check(st)
+        return res
+
+    def query(self) -> ServerInfo:
+        info = ServerInfo()
+        _check(load().cbct_server_query(self.handle, ctypes.byref(info)))
+        return info
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            load().cbct_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()
+
+
+def pinned_stats_buffer():
+    """A page-locked byte buffer for one cbct_recon_stats (serving)."""
+    import torch
+    return torch.zeros(ctypes.sizeof(ReconStats), dtype=torch.uint8).pin_memory()
+
+
+def read_host_stats(buf) -> ReconStats:
+    return ReconStats.from_buffer_copy(bytes(buf.numpy().tobytes()))
+

@@ -56,6 +56,7 @@ struct ProfSlot {
     cudaEvent_t start, stop;
 };
 bool g_prof_on = false;
+thread_local bool t_quiet = false;   // threads whose launches the profiler skips
 std::vector<ProfSlot> g_pool;
 size_t g_pool_used = 0;
 int64_t g_prof_count[K_COUNT] = {};
@@ -69,7 +70,7 @@ namespace cbct {
 void launch_begin(int kernel, cudaStream_t s)
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (!g_prof_on) return;
+    if (!g_prof_on || t_quiet) return;
     if (g_pool_used == g_pool.size()) {
         ProfSlot p{};
         if (cudaEventCreate(&p.start) != cudaSuccess || cudaEventCreate(&p.stop) != cudaSuccess) return;
@@ -82,9 +83,11 @@ void launch_begin(int kernel, cudaStream_t s)
 
 void note_extra_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+void set_thread_quiet(bool quiet) { t_quiet = quiet; }
+
 void launch_end(int kernel, cudaStream_t s)
 {
-    if (!g_prof_on) return;
+    if (!g_prof_on || t_quiet) return;
     if (g_pool_used < g_pool.size() && g_pool[g_pool_used].kernel == kernel) {
         cudaEventRecord(g_pool[g_pool_used].stop, s);
         g_pool_used++;
@@ -104,6 +107,7 @@ struct LevelData {
 };
 
 struct cbct_geometry {
+    uint64_t serial;           // unique per created geometry
     cbct_geometry_desc desc;
     std::vector<double> angles;
     int device;
@@ -208,6 +212,8 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
     if (st != CBCT_OK) return st;
     cbct_geometry *G = new (std::nothrow) cbct_geometry();
     if (!G) return fail(CBCT_ERR_OUT_OF_MEMORY, "host allocation failed");
+    static std::atomic<uint64_t> next_serial{1};
+    G->serial = next_serial.fetch_add(1);
     G->desc = *desc;
     if (G->desc.step_ratio == 0) G->desc.step_ratio = 0.5;
     G->angles.assign(desc->angles, desc->angles + desc->n_views);
@@ -919,6 +925,7 @@ const VolGeom *geometry_level(const cbct_geometry *g, int level)
 }
 const DetGeom *geometry_detector(const cbct_geometry *g) { return g ? &g->det : nullptr; }
 int geometry_device(const cbct_geometry *g) { return g ? g->device : -1; }
+uint64_t geometry_serial(const cbct_geometry *g) { return g ? g->serial : 0; }
 cbct_status report_error(cbct_status st, const char *msg)
 {
     if (st == CBCT_OK) return ok();

@@ -266,6 +266,7 @@ cudaError_t launch_rof(const RofArgs &a, cudaStream_t s);
 const VolGeom *geometry_level(const cbct_geometry *g, int level);
 const DetGeom *geometry_detector(const cbct_geometry *g);
 int geometry_device(const cbct_geometry *g);
+uint64_t geometry_serial(const cbct_geometry *g);  // unique per created geometry
 cbct_status report_error(cbct_status st, const char *msg);
 
 } // namespace cbct

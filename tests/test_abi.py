@@ -92,8 +92,9 @@ def test_struct_layouts_match_header_sizes():
     code = """
 #include <stdio.h>
 #include "cbct.h"
-int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(cbct_geometry_desc), sizeof(cbct_tv_params),
- sizeof(cbct_tv_stats), sizeof(cbct_recon_params), sizeof(cbct_iter_stats), sizeof(cbct_recon_stats));return 0;}
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cbct_geometry_desc), sizeof(cbct_tv_params),
+ sizeof(cbct_tv_stats), sizeof(cbct_recon_params), sizeof(cbct_iter_stats), sizeof(cbct_recon_stats),
+ sizeof(cbct_server_config), sizeof(cbct_scan_result), sizeof(cbct_server_info));return 0;}
 """
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "probe.c")
@@ -102,5 +103,6 @@ int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(cbct_geometry_desc), 
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         sizes = [int(x) for x in subprocess.check_output([exe]).split()]
     mine = [ctypes.sizeof(t) for t in (cbct.GeometryDesc, cbct.TvParams, cbct.TvStats, cbct.ReconParams,
-                                       cbct.IterStats, cbct.ReconStats)]
+                                       cbct.IterStats, cbct.ReconStats, cbct.ServerConfig, cbct.ScanResult,
+                                       cbct.ServerInfo)]
     assert sizes == mine

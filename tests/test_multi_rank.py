@@ -29,7 +29,7 @@ def _worker(rank, world, port, out):
 def test_two_ranks_time_is_max_over_ranks_and_scans_differ():
     torch = pytest.importorskip("torch")
     import torch.multiprocessing as mp
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     port = _free_port()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
