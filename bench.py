@@ -57,9 +57,13 @@ def parse():
                     help="Step 1 gradient: matched transpose P^T or the paper's closed form (Eq. 6)")
     ap.add_argument("--level", type=int, default=0,
                     help="one-iteration mode: multigrid level (0 = finest)")
-    ap.add_argument("--mode", default="recon", choices=["recon", "one-iteration"],
+    ap.add_argument("--mode", default="recon", choices=["recon", "one-iteration", "serve"],
                     help="one-iteration: each step is one FBS iteration on the finest grid with a "
-                         "given step (per-kernel timing and profiler captures)")
+                         "given step (per-kernel timing and profiler captures); serve: a stream of "
+                         "mixed scans through the serving runtime (latency percentiles, throughput)")
+    ap.add_argument("--serve-scans", type=int, default=64, help="serve mode: scans in the stream")
+    ap.add_argument("--serve-loads", default="0.5,0.8,1.0",
+                    help="serve mode: arrival rates as fractions of the sequential capacity")
     return ap.parse_args()
 
 
@@ -224,6 +228,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.mode == "serve":
+        return serve_bench(args, rank, world, local)
 
     import numpy as np
     import torch
@@ -379,6 +385,173 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# serving: a stream of mixed scans
+# ---------------------------------------------------------------------------
+SERVE_GRIDS = [(128, 128, 128, 2.0, 2.0, 2.0), (192, 192, 128, 4.0 / 3.0, 4.0 / 3.0, 1.0),
+               (256, 256, 128, 1.0, 1.0, 1.0), (256, 256, 256, 1.0, 1.0, 1.0)]
+SERVE_DETECTORS = [(512, 384, 0.78, 0.78), (256, 192, 1.56, 1.56)]
+SERVE_VIEWS = [20, 40, 60, 90]
+SERVE_ITERS = (20, 15, 15)
+
+
+def serve_stream(n_scans: int, seed: int = 10):
+    """The scan mix: grid, detector and view count drawn uniformly per scan."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(len(SERVE_GRIDS))), int(rng.integers(len(SERVE_DETECTORS))),
+             int(rng.integers(len(SERVE_VIEWS)))) for _ in range(n_scans)]
+
+
+def fifo_latencies(arrivals, service):
+    """Latencies of a one-at-a-time FIFO server with the given service times."""
+    t, out = 0.0, []
+    for a, s in zip(arrivals, service):
+        t = max(t, a) + s
+        out.append(t - a)
+    return out
+
+
+def serve_bench(args, rank, world, local):
+    """Serving benchmark (no counterpart in the paper): --serve-scans scans
+    drawn from 4 grids x 2 detectors x 4 view counts, each reconstructed with
+    50 FBS-TV iterations (3-level multigrid 20/15/15), arriving as a Poisson
+    stream at several fractions of the sequential capacity. The sequential
+    system processes one scan at a time through cbct_reconstruct_host (copy
+    in, reconstruct, copy out, wait); the server overlaps copies with compute
+    and replays captured graphs. Outputs are checked bit-identical between
+    the two, so the RMS error is equal by construction."""
+    import hashlib
+
+    import numpy as np
+    import torch
+
+    from paper_1001_0599_gb300 import build as lib_build
+    lib_build.build()
+    from paper_1001_0599_gb300 import cbct, synthetic
+
+    torch.cuda.set_device(local)
+    stream = serve_stream(args.serve_scans)
+    tv = cbct.TvParams.paper(eps_tv=1e-5)
+    params = cbct.make_recon_params(0.05, SERVE_ITERS, tv, power_iters=20, clamp=True, power_iters_fine=4)
+    geoms, truths, scans = {}, {}, []
+    for i, (gi, di, vi) in enumerate(stream):
+        nx, ny, nz, dx, dy, dz = SERVE_GRIDS[gi]
+        nu, nv, du, dv = SERVE_DETECTORS[di]
+        key = (gi, di, vi)
+        if key not in geoms:
+            wl = synthetic.Workload(f"serve{gi}{di}{vi}", nx, ny, nz, dx, dy, dz, nu, nv, du, dv, SERVE_VIEWS[vi],
+                                    photons=5e4, phantom="head_neck", phantom_seed=3, noise_seed=10,
+                                    lam=0.05, iters=SERVE_ITERS)
+            geoms[key] = (wl, cbct.geometry_from_workload(wl))
+        wl, g = geoms[key]
+        if gi not in truths:
+            truths[gi] = synthetic.voxelise(synthetic.make_phantom(wl), nx, ny, nz, dx, dy, dz).astype(np.float32)
+        # measured line integrals: projector of the voxelised phantom, Poisson counts
+        p = torch.empty(g.sino_shape, device="cuda")
+        cbct.cbct_forward_project(g, torch.from_numpy(truths[gi]).cuda(), p)
+        gen = torch.Generator(device="cuda").manual_seed(10_000 + i)
+        counts = torch.poisson(wl.photons * torch.exp(-p), generator=gen)
+        y = torch.log(wl.photons / counts.clamp_min(1.0)).float()
+        scans.append((key, g, y.cpu().contiguous().pin_memory(), gi))
+    torch.cuda.synchronize()
+
+    # sequential plain FP32: one scan at a time through the host-buffer entry point
+    ws = {key: cbct.workspace(cbct.cbct_workspace_size_host(g, params)) for key, (wl, g) in geoms.items()}
+    h_out = torch.empty(max(int(np.prod(g.vol_shape)) for _, g in geoms.values()), dtype=torch.float32).pin_memory()
+    for key, (wl, g) in geoms.items():   # warm-up: one scan per shape
+        first = next(s for s in scans if s[0] == key)
+        cbct.cbct_reconstruct_host(g, first[2].numpy(), h_out[:int(np.prod(g.vol_shape))].numpy(), params, ws[key])
+    service, digests, rms = [], [], []
+    t_all = time.perf_counter()
+    for key, g, y, gi in scans:
+        n = int(np.prod(g.vol_shape))
+        t0 = time.perf_counter()
+        cbct.cbct_reconstruct_host(g, y.numpy(), h_out[:n].numpy(), params, ws[key])
+        service.append(time.perf_counter() - t0)
+        out = h_out[:n].numpy()
+        digests.append(hashlib.sha1(out.tobytes()).hexdigest())
+        rms.append(float(np.sqrt(np.mean((out.reshape(g.vol_shape) - truths[gi]) ** 2))))
+    seq_total = time.perf_counter() - t_all
+    del ws
+    torch.cuda.empty_cache()
+    capacity = len(scans) / sum(service)     # scans per second, one at a time
+
+    results = []
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    srv = cbct.Server(use_graphs=True)
+    outs = [torch.empty(g.vol_shape, dtype=torch.float32).pin_memory() for _, g, _, _ in scans]
+    # warm-up: one scan per shape captures its slot's graph
+    warm = [srv.submit(g, params, scans[[s[0] for s in scans].index(key)][2], outs[0].new_empty(g.vol_shape).pin_memory())
+            for key, (wl, g) in geoms.items()]
+    for t in warm:
+        srv.wait(t)
+    identical = True
+    sampler.start()
+    for load in [float(x) for x in args.serve_loads.split(",") if x]:
+        rate = load * capacity
+        arr = np.cumsum(np.random.default_rng(10).exponential(1.0 / rate, len(scans)))
+        arr -= arr[0]
+        tickets = []
+        t0 = time.perf_counter()
+        for (key, g, y, gi), a, o in zip(scans, arr, outs):
+            delay = t0 + a - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(g, params, y, o))
+        res = [srv.wait(t) for t in tickets]
+        lat = [r.t_done - r.t_submit for r in res]
+        span = max(r.t_done for r in res) - min(r.t_submit for r in res)
+        for o, dgst in zip(outs, digests):
+            identical &= hashlib.sha1(o.numpy().tobytes()).hexdigest() == dgst
+        seq_lat = fifo_latencies(list(arr), service)
+        results.append({"load": load, "arrivals_per_s": rate,
+                        "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                        "scans_per_min": 60.0 * len(scans) / span,
+                        "sequential_p50_s": float(np.percentile(seq_lat, 50)),
+                        "sequential_p99_s": float(np.percentile(seq_lat, 99)),
+                        "gpu_s_per_scan": float(np.mean([r.gpu_ms for r in res]) / 1e3),
+                        "graph_replays": int(sum(r.graph_replay for r in res))})
+    clocks = sampler.stop()
+    info = srv.query()
+    srv.close()
+    # back-to-back stream (all scans submitted at once): the throughput ceiling
+    srv = cbct.Server(use_graphs=True)
+    for t in [srv.submit(g, params, scans[[s[0] for s in scans].index(key)][2],
+                         outs[0].new_empty(g.vol_shape).pin_memory()) for key, (wl, g) in geoms.items()]:
+        srv.wait(t)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(g, params, y, o) for (key, g, y, gi), o in zip(scans, outs)]
+    res = [srv.wait(t) for t in tickets]
+    burst = time.perf_counter() - t0
+    srv.close()
+    line = {"metric": "serving: scan latency p50/p99 (s) and scans/min, mixed 64-scan stream",
+            "mode": "serve", "value": results[-1]["p99_s"] if results else None, "unit": "s (p99 at the highest load)",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{len(scans)} scans; grids {SERVE_GRIDS}; detectors {SERVE_DETECTORS}; "
+                                   f"views {SERVE_VIEWS}; 50 FBS-TV iterations (multigrid 20/15/15), "
+                                   "lambda 0.05, Poisson 5e4 photons; stream seed 10",
+                       "arrivals": "Poisson at the listed fractions of the sequential capacity"},
+            "sequential": {"scans_per_min": 60.0 * capacity, "total_s": seq_total,
+                           "mean_service_s": float(np.mean(service))},
+            "server_burst": {"scans_per_min": 60.0 * len(scans) / burst, "total_s": burst},
+            "loads": results, "bit_identical_to_sequential": bool(identical),
+            "rms_error_vs_phantom": float(np.mean(rms)),
+            "server": {"slots": int(info.slots), "graphs_captured": int(info.graphs_captured),
+                       "graph_failures": int(info.graph_failures), "evictions": int(info.evictions),
+                       "peak_arena_gb": info.peak_bytes_in_use / 1e9, "arena_gb": info.arena_bytes / 1e9},
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 

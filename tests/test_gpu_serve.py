@@ -1,0 +1,152 @@
+"""The serving runtime: every served scan equals, bit for bit, the same scan
+reconstructed directly with cbct_reconstruct (whose parity with the oracle the
+reconstruction tests establish), whether it runs directly or as a graph
+replay, in a fresh or a reused slot, under a tight arena that forces
+evictions, and with one resident slot."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from gpu_util import CASES
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_1001_0599_gb300 import build, cbct
+    build.build()
+    cbct.load()
+    assert torch.cuda.is_available()
+    return cbct
+
+
+def _scans(lib, names, n_each, seed=0):
+    """(geometry, params, pinned sinogram) triples with seeded noisy inputs."""
+    import torch
+    from paper_1001_0599_gb300 import synthetic
+    rng = np.random.default_rng(seed)
+    out = []
+    geoms = {}
+    for name in names:
+        wl = CASES[name] if name in CASES else synthetic.workload(name)
+        geoms[name] = (wl, lib.geometry_from_workload(wl))
+    tv = lib.TvParams.paper()
+    for k in range(n_each):
+        for name in names:
+            wl, g = geoms[name]
+            try:
+                g.level_dims(1)
+                levels = (3, 2)
+            except lib.CbctError:
+                levels = (4,)
+            params = lib.make_recon_params(0.02, levels, tv, power_iters=10, clamp=True, power_iters_fine=2)
+            truth = np.asarray(rng.random((wl.nx, wl.ny, wl.nz)), dtype=np.float32) * 0.02
+            f = torch.from_numpy(truth).cuda()
+            p = torch.empty(g.sino_shape, device="cuda")
+            lib.cbct_forward_project(g, f, p)
+            noisy = p + 0.01 * torch.randn(p.shape, device="cuda",
+                                           generator=torch.Generator("cuda").manual_seed(seed * 1000 + k))
+            out.append((name, g, params, noisy.cpu().contiguous().pin_memory()))
+    return out
+
+
+def _direct(lib, g, params, h_sino):
+    import torch
+    ws = lib.workspace(lib.cbct_workspace_size(g, params))
+    st = lib.stats_buffer()
+    vol = torch.zeros(g.vol_shape, device="cuda")
+    lib.cbct_reconstruct(g, h_sino.cuda(), vol, params, ws, st)
+    torch.cuda.synchronize()
+    return vol.cpu().numpy(), lib.read_stats(st)
+
+
+def _serve(lib, scans, **cfg):
+    import torch
+    srv = lib.Server(**cfg)
+    outs = []
+    tickets = []
+    for name, g, params, h_sino in scans:
+        h_vol = torch.empty(g.vol_shape).pin_memory()
+        h_st = lib.pinned_stats_buffer()
+        tickets.append(srv.submit(g, params, h_sino, h_vol, h_st))
+        outs.append((h_vol, h_st))
+    results = [srv.wait(t) for t in tickets]
+    info = srv.query()
+    srv.close()
+    return [(v.numpy().copy(), lib.read_host_stats(s)) for v, s in outs], results, info
+
+
+def test_served_scans_equal_direct_reconstruction(lib):
+    scans = _scans(lib, ["small", "odd", "tall"], 2, seed=1)
+    ref = [_direct(lib, g, p, s) for _, g, p, s in scans]
+    for graphs in (True, False):
+        got, res, info = _serve(lib, scans, use_graphs=graphs)
+        assert info.completed == len(scans) and info.submitted == len(scans)
+        for (v, st), (rv, rst), r in zip(got, ref, res):
+            assert r.status == 0
+            assert np.array_equal(v, rv)
+            assert st.n_iters == rst.n_iters and st.flags == rst.flags
+            assert list(st.tau[:2]) == list(rst.tau[:2])
+            assert r.t_submit <= r.t_admit <= r.t_done and r.gpu_ms > 0
+        if graphs:
+            # one capture per slot: at least one slot per shape, at most one per scan
+            assert 3 <= info.graphs_captured + info.graph_failures <= len(scans)
+            if info.graph_failures == 0:
+                # every scan runs as one launch of its slot's captured graph
+                assert [r.graph_replay for r in res] == [1] * len(res)
+        else:
+            assert info.graphs_captured == 0 and all(r.graph_replay == 0 for r in res)
+
+
+def test_tight_arena_evicts_and_one_slot_serialises(lib):
+    scans = _scans(lib, ["small", "odd"], 3, seed=2)
+    ref = [_direct(lib, g, p, s) for _, g, p, s in scans]
+    sizes = []
+    for _, g, p, _s in scans[:2]:
+        sizes.append(lib.cbct_workspace_size(g, p) + 4 * (int(np.prod(g.sino_shape)) + int(np.prod(g.vol_shape))))
+    arena = int(max(sizes) * 1.3) + (1 << 16)
+    got, res, info = _serve(lib, scans, arena_bytes=arena, use_graphs=True)
+    assert info.peak_bytes_in_use <= info.arena_bytes
+    assert info.evictions > 0   # alternating shapes do not fit side by side
+    for (v, _), (rv, _), r in zip(got, ref, res):
+        assert r.status == 0 and np.array_equal(v, rv)
+    got, res, info = _serve(lib, scans, max_resident=1, use_graphs=True)
+    assert info.slots <= 1
+    for (v, _), (rv, _), r in zip(got, ref, res):
+        assert r.status == 0 and np.array_equal(v, rv)
+    # arrival order is kept
+    assert all(a.t_admit <= b.t_admit for a, b in zip(res, res[1:]))
+
+
+def test_submit_validation(lib):
+    import torch
+    from paper_1001_0599_gb300 import synthetic
+    wl = CASES["small"]
+    g = lib.geometry_from_workload(wl)
+    params = lib.make_recon_params(0.02, (2,), lib.TvParams.paper())
+    srv = lib.Server(arena_bytes=1 << 20)
+    pinned_s = torch.zeros(g.sino_shape).pin_memory()
+    pinned_v = torch.zeros(g.vol_shape).pin_memory()
+    with pytest.raises(ValueError):   # pageable host buffers are refused by the binding
+        srv.submit(g, params, torch.zeros(g.sino_shape), pinned_v)
+    # and by the library itself
+    t = ctypes.c_uint64()
+    page = np.zeros(g.sino_shape, dtype=np.float32)
+    st = lib.load().cbct_server_submit(srv.handle, g.handle, ctypes.byref(params), page.ctypes.data,
+                                       pinned_v.data_ptr(), None, ctypes.byref(t))
+    assert st == 1
+    # a slot larger than the whole arena is refused up front
+    with pytest.raises(lib.CbctError):
+        srv.submit(g, params, pinned_s, pinned_v)
+    with pytest.raises(lib.CbctError):
+        srv.wait(12345)
+    srv.close()
+    # replay schedules are for parity tests, not for served scans
+    srv = lib.Server()
+    rp = lib.make_recon_params(0.02, (1,), lib.TvParams.paper(), taus=[1e-3], replay=[[1]])
+    with pytest.raises(lib.CbctError):
+        srv.submit(g, rp, pinned_s, pinned_v)
+    srv.close()
