@@ -55,6 +55,11 @@ def parse():
                          "prolongated eigenvector of the previous level (0: 20 from ones everywhere)")
     ap.add_argument("--gradient", default="matched", choices=["matched", "eq6"],
                     help="Step 1 gradient: matched transpose P^T or the paper's closed form (Eq. 6)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp16"],
+                    help="storage type of the sinograms and of the projector's volume copy "
+                         "(FP32 arithmetic throughout)")
+    ap.add_argument("--workload", default="paper", choices=["paper", "lowdose"],
+                    help="paper: 256x256x128, 40 views; lowdose: 256^3, 360 views, 1e4 photons")
     ap.add_argument("--level", type=int, default=0,
                     help="one-iteration mode: multigrid level (0 = finest)")
     ap.add_argument("--mode", default="recon", choices=["recon", "one-iteration", "serve"],
@@ -244,7 +249,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    wl = synthetic.workload("paper")
+    wl = synthetic.workload(args.workload)
     truth, y = synthetic.make_problem(wl)
     if world > 1:  # each rank reconstructs its own scan (different noise draw)
         y = synthetic.poisson_log_sinogram(synthetic.exact_sinogram(synthetic.make_phantom(wl), wl),
@@ -256,7 +261,8 @@ def main():
         params = cbct.make_recon_params(wl.lam, iters, tv, taus=[1.28e-5] * (args.level + 1), clamp=True)
     else:
         params = cbct.make_recon_params(wl.lam, wl.iters, tv, power_iters=20, clamp=True,
-                                        power_iters_fine=args.power_fine, gradient=args.gradient)
+                                        power_iters_fine=args.power_fine, gradient=args.gradient,
+                                        storage=args.storage)
     ws = cbct.workspace(cbct.cbct_workspace_size(g, params))
     stats = cbct.stats_buffer()
     d_y = torch.from_numpy(y.astype(np.float32)).cuda()
@@ -360,9 +366,18 @@ def main():
         f"warm-started from the prolongated eigenvector)")
     if args.gradient == "eq6":
         workload += "; Step 1 gradient from the paper's closed form (Eq. 6) instead of the matched transpose"
-    line = {"metric": METRIC, "value": sec_per_scan, "unit": "s", "n_gpus": world, "steps": args.steps,
+    metric = METRIC
+    if args.workload == "lowdose":
+        workload = workload.replace("paper-scale: 256x256x128 voxels", "low-dose: 256x256x256 voxels").replace(
+            "40 views/360 deg", "360 views/360 deg").replace("Poisson 5e4", "Poisson 1e4")
+        metric = "recon sec at 256^3 x 360 views (low-dose workload)"
+    if args.storage != "f32":
+        workload += (f"; measured sinogram, residual and the projector's volume copy stored as {args.storage} "
+                     "(FP32 arithmetic, FP64 sums)")
+    line = {"metric": metric, "value": sec_per_scan, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32 ({args.storage} storage)",
+            "data": "synthetic",
             "config": {"workload": workload, "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "reductions": "FP64 across blocks, compensated FP32 within"},
@@ -581,7 +596,7 @@ def roofline(prof, wl, steps, clocks):
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     try:
         with open(os.path.join(ROOT, "tests", "golden", "nnz.json")) as fh:
-            nnz = json.load(fh)["paper"]
+            nnz = json.load(fh)[wl.name]
     except (OSError, KeyError, ValueError):
         nnz = None
     levels = len(wl.iters)

@@ -43,6 +43,17 @@ typedef enum {
     CBCT_ERR_TIMEOUT = 7               /* a bounded device-side wait gave up (stats.status) */
 } cbct_status;
 
+/* Storage type of a volume or sinogram array for the reduced-precision
+ * entry points and cbct_recon_params.storage (no counterpart in the paper,
+ * which stores FP32): values widen to FP32 on every load and round to
+ * nearest on every store; interpolation and accumulation stay FP32 and
+ * reductions FP64. */
+typedef enum {
+    CBCT_STORAGE_F32 = 0,
+    CBCT_STORAGE_BF16 = 1,   /* bfloat16: 8-bit significand, FP32 range */
+    CBCT_STORAGE_F16 = 2     /* IEEE binary16: 11-bit significand, max 65504 */
+} cbct_storage;
+
 /* Opaque geometry handle: validated copy of the description plus per-level
  * ray tables (FP64-derived, stored FP32) on the device that was current at
  * creation. Only that device may use it. */
@@ -108,6 +119,9 @@ typedef struct {
      * searching. NULL for normal operation. */
     const int32_t *replay;
     int replay_len;
+    int storage;                     /* cbct_storage of the measured sinogram, the residual and
+                                        the volume copy the projector gathers from (the iterate
+                                        itself, its ROF state and all sums stay FP32/FP64) */
 } cbct_recon_params;
 
 typedef struct {
@@ -194,6 +208,21 @@ cbct_status cbct_eq6_gradient(const cbct_geometry *geom, const float *d_T, float
  * d_g may alias neither d_f nor d_r. */
 cbct_status cbct_gradient_step(const cbct_geometry *geom, const float *d_r, const float *d_f,
                                float *d_g, double scale, void *stream);
+
+/* ---- reduced-precision storage ----------------------------------------- */
+
+/* P (Eq. 1) of a volume stored as `storage` into a sinogram stored the same
+ * way (FP32 arithmetic in between). Reduced storage needs the shared-memory
+ * sheet projector (nv <= 1024 and nz <= 764); otherwise CBCT_ERR_UNSUPPORTED. */
+cbct_status cbct_forward_project_ex(const cbct_geometry *geom, const void *d_vol, void *d_sino, int storage,
+                                    void *stream);
+/* The matched transpose of a sinogram stored as `storage`, into an FP32
+ * volume (overwritten). */
+cbct_status cbct_back_project_ex(const cbct_geometry *geom, const void *d_sino, int storage, float *d_vol,
+                                 void *stream);
+/* n elements from src_storage to dst_storage (round to nearest). */
+cbct_status cbct_convert(const void *d_src, int src_storage, void *d_dst, int dst_storage, size_t n,
+                         void *stream);
 
 /* ---- TV / ROF (Sec. II.B) ---------------------------------------------- */
 

@@ -354,6 +354,50 @@ def fbs_iteration(g: Geometry, y, f, lam: float, tau: float, p: TVParams, clamp:
     return e2.value, st, log[: st.n_inner].copy()
 
 
+def round_storage(x, storage: str) -> np.ndarray:
+    """Round values to a storage type and widen back to FP64, as a store and a
+    later load do: first to FP32 (nearest even), then to bfloat16 (the upper
+    16 bits of the FP32 pattern, nearest even) or IEEE binary16 (nearest even)."""
+    x32 = np.asarray(x, dtype=np.float64).astype(np.float32)
+    if storage == "f32":
+        return x32.astype(np.float64)
+    if storage == "fp16":
+        with np.errstate(over="ignore"):   # beyond 65504 rounds to infinity, as IEEE stores do
+            return x32.astype(np.float16).astype(np.float64)
+    if storage == "bf16":
+        u = x32.view(np.uint32).astype(np.uint64)
+        u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+        return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    raise ValueError(storage)
+
+
+def ray_ds(g: Geometry) -> np.ndarray:
+    """Sample spacing along each ray, Delta rho L(u, v) / L_xy(u), per (iv, iu)
+    (the same for every view): the weight every sample of P carries."""
+    u = (np.arange(g.nu) - 0.5 * (g.nu - 1)) * g.du
+    v = (np.arange(g.nv) - 0.5 * (g.nv - 1)) * g.dv
+    lxy = np.sqrt(g.sdd ** 2 + u[None, :] ** 2)
+    return drho(g) * np.sqrt(lxy ** 2 + v[:, None] ** 2) / lxy
+
+
+def fbs_iteration_storage(g: Geometry, y_stored, f, lam: float, tau: float, p: TVParams, storage: str,
+                          clamp: bool = True, replay: Optional[Sequence[int]] = None):
+    """Algorithm A1 iteration with the projector reading a copy of f rounded to
+    ``storage``, the measured sinogram already rounded (``y_stored``), and the
+    residual stored, pre-weighted by the sample spacing, rounded to
+    ``storage``; everything else FP64. In place on f."""
+    fq = round_storage(f, storage)
+    r = forward_project(g, fq) - y_stored
+    e2 = float(np.mean(r * r))
+    ds = ray_ds(g)[None, :, :]
+    r_stored = round_storage(ds * r, storage) / ds
+    gaux = f - tau * kappa(g) * back_project(g, r_stored)
+    res = rof_solve(g, gaux, lam, tau, p, replay=replay)
+    f[...] = np.maximum(res.f, 0.0) if clamp else res.f
+    st = _RofStats(res.n_inner, res.flags, res.e_first, res.e_last)
+    return e2, st, res.log
+
+
 @dataclasses.dataclass
 class ReconResult:
     f: np.ndarray
@@ -369,7 +413,7 @@ def reconstruct(g: Geometry, y, lam: float, iters: Sequence[int], p: TVParams,
                 taus: Optional[Sequence[float]] = None, power_iters: int = 20,
                 clamp: bool = True, f_init=None,
                 replay: Optional[Sequence[Sequence[int]]] = None,
-                power_iters_fine: int = 0, gradient: str = "matched") -> ReconResult:
+                power_iters_fine: int = 0, gradient: str = "matched", storage: str = "f32") -> ReconResult:
     """Algorithm A1 under the coarse-to-fine schedule of Sec. II.C.3.
 
     ``iters`` lists the FBS iterations per level, coarsest first; level l of
@@ -380,9 +424,11 @@ def reconstruct(g: Geometry, y, lam: float, iters: Sequence[int], p: TVParams,
     power iterations on kappa P^T P started from ones; with
     ``power_iters_fine`` > 0, every level after the first instead runs that
     many iterations started from the prolongation of the previous level's
-    last iterate.
+    last iterate. With ``storage`` other than "f32" every iteration is
+    fbs_iteration_storage on the measured sinogram rounded once.
     """
     y = _f64(y)
+    y_stored = round_storage(y, storage) if storage != "f32" else None
     n_levels = len(iters)
     f = None
     out_taus, logs = [], []
@@ -406,8 +452,11 @@ def reconstruct(g: Geometry, y, lam: float, iters: Sequence[int], p: TVParams,
         out_taus.append(tau)
         for _ in range(iters[lev]):
             rep = replay[k] if replay is not None else None
-            step = fbs_iteration_eq6 if gradient == "eq6" else fbs_iteration
-            e2, st, steps = step(gl, y, f, lam, tau, p, clamp, rep)
+            if y_stored is not None:
+                e2, st, steps = fbs_iteration_storage(gl, y_stored, f, lam, tau, p, storage, clamp, rep)
+            else:
+                step = fbs_iteration_eq6 if gradient == "eq6" else fbs_iteration
+                e2, st, steps = step(gl, y, f, lam, tau, p, clamp, rep)
             logs.append(IterLog(lev, e2, st.n_inner, st.flags, st.e_first, st.e_last,
                                 [int(s) for s in steps]))
             k += 1

@@ -62,7 +62,8 @@ class ReconParams(ctypes.Structure):
                 ("iters", ctypes.c_int * CBCT_MAX_LEVELS), ("tau", ctypes.c_double * CBCT_MAX_LEVELS),
                 ("power_iters", ctypes.c_int), ("clamp", ctypes.c_int), ("power_iters_fine", ctypes.c_int),
                 ("gradient_mode", ctypes.c_int), ("tv", TvParams),
-                ("replay", ctypes.POINTER(ctypes.c_int32)), ("replay_len", ctypes.c_int)]
+                ("replay", ctypes.POINTER(ctypes.c_int32)), ("replay_len", ctypes.c_int),
+                ("storage", ctypes.c_int)]
 
 
 class IterStats(ctypes.Structure):
@@ -122,6 +123,12 @@ def load() -> ctypes.CDLL:
     L.cbct_residual_static.restype = st
     L.cbct_back_project.argtypes = [_P, _P, _P, _P]
     L.cbct_back_project.restype = st
+    L.cbct_forward_project_ex.argtypes = [_P, _P, _P, ctypes.c_int, _P]
+    L.cbct_forward_project_ex.restype = st
+    L.cbct_back_project_ex.argtypes = [_P, _P, ctypes.c_int, _P, _P]
+    L.cbct_back_project_ex.restype = st
+    L.cbct_convert.argtypes = [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_size_t, _P]
+    L.cbct_convert.restype = st
     L.cbct_eq6_gradient.argtypes = [_P, _P, _P, _P]
     L.cbct_eq6_gradient.restype = st
     L.cbct_gradient_step.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
@@ -278,6 +285,39 @@ def cbct_back_project(geom: Geometry, sino, vol, stream=None) -> None:
     _check(load().cbct_back_project(geom.handle, _f32(sino, "sino"), _f32(vol, "vol"), _stream(stream)))
 
 
+STORAGE = {"f32": 0, "bf16": 1, "fp16": 2}
+
+
+def _storage_of(t):
+    import torch
+    m = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
+    if not isinstance(t, torch.Tensor) or t.dtype not in m:
+        raise TypeError("storage tensors must be float32, bfloat16 or float16")
+    return m[t.dtype]
+
+
+def cbct_forward_project_ex(geom: Geometry, vol, sino, stream=None) -> None:
+    """P with the volume and sinogram stored as float32, bfloat16 or float16
+    (both the same type; FP32 arithmetic)."""
+    st = _storage_of(vol)
+    if _storage_of(sino) != st:
+        raise TypeError("vol and sino must share a storage type")
+    _check(load().cbct_forward_project_ex(geom.handle, _dev(vol, "vol"), _dev(sino, "sino"), st, _stream(stream)))
+
+
+def cbct_back_project_ex(geom: Geometry, sino, vol, stream=None) -> None:
+    """Matched transpose of a float32/bfloat16/float16 sinogram into a float32 volume."""
+    _check(load().cbct_back_project_ex(geom.handle, _dev(sino, "sino"), _storage_of(sino), _f32(vol, "vol"),
+                                       _stream(stream)))
+
+
+def cbct_convert(src, dst, stream=None) -> None:
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst sizes differ")
+    _check(load().cbct_convert(_dev(src, "src"), _storage_of(src), _dev(dst, "dst"), _storage_of(dst),
+                               src.numel(), _stream(stream)))
+
+
 def cbct_eq6_gradient(geom: Geometry, T, vol, stream=None) -> None:
     _check(load().cbct_eq6_gradient(geom.handle, _f32(T, "T"), _f32(vol, "vol"), _stream(stream)))
 
@@ -319,8 +359,10 @@ def cbct_power_lipschitz(geom: Geometry, level: int, n_iter: int, out, ws, strea
 def make_recon_params(lam: float, iters: Sequence[int], tv: Optional[TvParams] = None,
                       taus: Optional[Sequence[float]] = None, power_iters: int = 20, clamp: bool = True,
                       replay: Optional[Sequence[Sequence[int]]] = None,
-                      power_iters_fine: int = 0, gradient: str = "matched") -> ReconParams:
-    """ReconParams; ``replay`` is a list of per-iteration step-reduction lists."""
+                      power_iters_fine: int = 0, gradient: str = "matched", storage: str = "f32") -> ReconParams:
+    """ReconParams; ``replay`` is a list of per-iteration step-reduction lists;
+    ``storage`` ("f32", "bf16", "fp16") is the type of the stored sinograms and
+    of the projector's volume copy."""
     p = ReconParams()
     p.lambda_ = lam
     p.n_levels = len(iters)
@@ -331,6 +373,7 @@ def make_recon_params(lam: float, iters: Sequence[int], tv: Optional[TvParams] =
     p.clamp = 1 if clamp else 0
     p.power_iters_fine = power_iters_fine
     p.gradient_mode = {"matched": 0, "eq6": 1}[gradient]
+    p.storage = STORAGE[storage]
     p.tv = tv if tv is not None else TvParams.paper()
     if replay is not None:
         flat = []

@@ -368,7 +368,8 @@ static double kappa_of(const VolGeom &v, const DetGeom &d) { return 2.0 * (doubl
 // workspace
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t state, partials, r, g, d, split, eig, coarse[CBCT_MAX_LEVELS], replay, stats, hsino, hvol, total;
+    size_t state, partials, r, g, d, split, eig, coarse[CBCT_MAX_LEVELS], replay, stats, hsino, hvol, ysto, fsto,
+        total;
     int n_partials;
 };
 
@@ -407,6 +408,14 @@ static Layout layout(const cbct_geometry *G, const cbct_recon_params *p, bool ho
     }
     L.replay = off;
     if (p && p->replay && p->replay_len > 0) off = align_up(off + sizeof(int32_t) * (size_t)p->replay_len);
+    // reduced storage: the measured sinogram and the projector's volume copy
+    L.ysto = L.fsto = off;
+    if (p && p->storage != CBCT_STORAGE_F32) {
+        L.ysto = off;
+        off = align_up(off + 2 * nray(G->det));
+        L.fsto = off;
+        off = align_up(off + 2 * nvox(v0));
+    }
     if (host_variant) {
         L.stats = off;
         off = align_up(off + sizeof(cbct_recon_stats));
@@ -489,6 +498,49 @@ extern "C" cbct_status cbct_back_project(const cbct_geometry *G, const float *d_
     CHECK(check_ptr(d_vol, "d_vol"));
     CUDA_TRY(launch_back(G->lev[0].vg, G->det, d_sino, nullptr, d_vol, nullptr, 0.0, 0.0, nullptr, 0, 0, nullptr,
                          (cudaStream_t)stream));
+    return ok();
+}
+
+static cbct_status check_storage(int st)
+{
+    if (st < CBCT_STORAGE_F32 || st > CBCT_STORAGE_F16)
+        return fail(CBCT_ERR_INVALID_ARG, "storage must be a cbct_storage value");
+    return CBCT_OK;
+}
+
+extern "C" cbct_status cbct_forward_project_ex(const cbct_geometry *G, const void *d_vol, void *d_sino, int storage,
+                                               void *stream)
+{
+    CHECK(check_geom(G));
+    CHECK(check_ptr(d_vol, "d_vol"));
+    CHECK(check_ptr(d_sino, "d_sino"));
+    CHECK(check_storage(storage));
+    if (!fp_supports_storage(G->lev[0].vg, G->det, storage))
+        return fail(CBCT_ERR_UNSUPPORTED, "reduced storage needs nv <= 1024 and nz <= 764");
+    CUDA_TRY(launch_forward_st(G->lev[0].vg, G->det, d_vol, nullptr, d_sino, storage, nullptr, nullptr, 0,
+                               (cudaStream_t)stream));
+    return ok();
+}
+
+extern "C" cbct_status cbct_back_project_ex(const cbct_geometry *G, const void *d_sino, int storage, float *d_vol,
+                                            void *stream)
+{
+    CHECK(check_geom(G));
+    CHECK(check_ptr(d_sino, "d_sino"));
+    CHECK(check_ptr(d_vol, "d_vol"));
+    CHECK(check_storage(storage));
+    CUDA_TRY(launch_back_st(G->lev[0].vg, G->det, d_sino, storage, nullptr, d_vol, nullptr, 0.0, 0.0, nullptr, 0, 0,
+                            nullptr, (cudaStream_t)stream));
+    return ok();
+}
+
+extern "C" cbct_status cbct_convert(const void *d_src, int src_storage, void *d_dst, int dst_storage, size_t n,
+                                    void *stream)
+{
+    CHECK(check_storage(src_storage));
+    CHECK(check_storage(dst_storage));
+    if (n > 0 && (!d_src || !d_dst)) return fail(CBCT_ERR_INVALID_ARG, "NULL device pointer");
+    CUDA_TRY(launch_convert(d_src, src_storage, d_dst, dst_storage, n, (cudaStream_t)stream));
     return ok();
 }
 
@@ -730,6 +782,14 @@ static cbct_status check_recon_params(const cbct_geometry *G, const cbct_recon_p
         return fail(CBCT_ERR_INVALID_ARG, "power_iters_fine out of range");
     if (p->gradient_mode != 0 && p->gradient_mode != 1)
         return fail(CBCT_ERR_INVALID_ARG, "gradient_mode must be 0 (matched P^T) or 1 (Eq. 6)");
+    if (p->storage < CBCT_STORAGE_F32 || p->storage > CBCT_STORAGE_F16)
+        return fail(CBCT_ERR_INVALID_ARG, "storage must be a cbct_storage value");
+    if (p->storage != CBCT_STORAGE_F32) {
+        if (p->gradient_mode != 0) return fail(CBCT_ERR_UNSUPPORTED, "reduced storage takes the matched gradient");
+        for (int l = 0; l < p->n_levels; l++)
+            if (!fp_supports_storage(G->lev[l].vg, G->det, p->storage))
+                return fail(CBCT_ERR_UNSUPPORTED, "reduced storage needs nv <= 1024 and nz <= 764");
+    }
     CHECK(check_tv_params(&p->tv));
     replay_off.clear();
     if (p->replay) {
@@ -766,6 +826,9 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
         d_replay = dr;
     }
     CUDA_TRY(launch_state_init(st, d_stats, s));
+    const int sto = p->storage;
+    void *ysto = at<void>(ws, L.ysto), *fsto = at<void>(ws, L.fsto);
+    if (sto != CBCT_STORAGE_F32) CUDA_TRY(launch_convert(d_sino, CBCT_STORAGE_F32, ysto, sto, nray(G->det), s));
     const int Lv = p->n_levels;
     const int power_iters = p->power_iters > 0 ? p->power_iters : 20;
     float *prev = nullptr;
@@ -801,6 +864,13 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
                 CUDA_TRY(launch_e2(partials, fp_partials_count(v, G->det), inv_m, st, s));
                 const double eq6_factor = (double)v.dx * v.dy * v.dz / (2.0 * (double)G->det.du * G->det.dv);
                 CUDA_TRY(launch_eq6(v, G->det, r, f, g, &st->scale, eq6_factor, 1, s));
+            } else if (sto != CBCT_STORAGE_F32) {
+                // Step 1 with y, r and the projector's copy of f stored as `sto`
+                CUDA_TRY(launch_convert(f, CBCT_STORAGE_F32, fsto, sto, nvox(v), s));
+                CUDA_TRY(launch_forward_st(v, G->det, fsto, ysto, r, sto, nullptr, partials, 2, s));
+                CUDA_TRY(launch_e2(partials, fp_partials_count(v, G->det), inv_m, st, s));
+                CUDA_TRY(launch_back_st(v, G->det, r, sto, f, g, &st->scale, 0.0, 0.0, nullptr, 1, 1,
+                                        at<float>(ws, L.split), s));
             } else {
                 // Step 1: r = ds (P f - y), E2; g = f - tau kappa P^T r
                 CUDA_TRY(launch_forward(v, G->det, f, d_sino, r, nullptr, partials, 2, s));

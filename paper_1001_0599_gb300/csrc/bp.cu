@@ -60,7 +60,8 @@ __host__ __device__ constexpr int bp_split_for(int nr) { return (nr == 0 || nr >
 struct BpLaunch {
     VolGeom v;
     DetGeom d;
-    const float *sino;
+    const void *sino;
+    int st;      // cbct_storage of sino
     const float *f;
     float *out;
     const double *d_scale;
@@ -103,8 +104,8 @@ __device__ __forceinline__ void box_u_range(const DetGeom &d, float c, float s, 
 // whose sample height is within one dz of z_c of (1 - sc |r - q|) * row value.
 template <int NR, bool PRESCALED>
 __device__ __forceinline__ float tent_rows(const DetGeom &d, const VolGeom &g, const float *pcol,
-                                           const float *gcol, const RayCol &rc, bool staged, int s0,
-                                           int s1, float q, float m, float sc)
+                                           const void *gsino, size_t gbase, int st, const RayCol &rc,
+                                           bool staged, int s0, int s1, float q, float m, float sc)
 {
     float s = 0.f;
     if (NR > 0 && staged) {
@@ -131,7 +132,7 @@ __device__ __forceinline__ float tent_rows(const DetGeom &d, const VolGeom &g, c
             if (staged && r >= s0 && r <= s1) {
                 val = pcol[r];
             } else {
-                val = __ldg(gcol + (size_t)r * d.nu);
+                val = ld_st(gsino, gbase + (size_t)r * d.nu, st);
                 if (!PRESCALED) {
                     const float vl = (((float)r - d.cv) * d.dv) * rc.inv_lxy;
                     val *= g.drho * sqrtf(1.f + vl * vl);
@@ -141,6 +142,32 @@ __device__ __forceinline__ float tent_rows(const DetGeom &d, const VolGeom &g, c
         }
     }
     return s;
+}
+
+// Stage rows [s0, s0 + h) x columns [iu0, iu0 + w) of one view's sinogram
+// into the column-major patch (pitch hp), zero outside the detector, weighted
+// by ds unless the sinogram is pre-weighted.
+template <bool PRESCALED, int NWARPS, typename T>
+__device__ __forceinline__ void stage_patch(float *patch, const T *__restrict__ src, const VolGeom &g, const DetGeom &d,
+                                            int view, int iu0, int s0, int w, int h, int hp, int wid, int lane)
+{
+    const int nu = d.nu, nv = d.nv;
+    for (int r = wid; r < h; r += NWARPS) {
+        const int iv = s0 + r;
+        const bool in = iv >= 0 && iv < nv;
+        for (int cc = lane; cc < w; cc += 32) {
+            const int iu = iu0 + cc;
+            float val = 0.f;
+            if (in) {
+                val = ldt(src + (size_t)iv * nu + iu);
+                if (!PRESCALED) {
+                    const float vl = (((float)iv - d.cv) * d.dv) * g.cols[(size_t)view * nu + iu].inv_lxy;
+                    val *= g.drho * sqrtf(1.f + vl * vl);
+                }
+            }
+            patch[cc * hp + r] = val;
+        }
+    }
 }
 
 // Staged variant only (no global fallback): NR rows from the padded patch.
@@ -198,7 +225,7 @@ __device__ __forceinline__ void add_corners(float (&acc)[BP_G][BP_G][ZC], float 
 // views and writes the raw sums to out + group * N_vox.
 template <int MODE, bool PRESCALED, int NR, int ZC, int SPLIT>
 __global__ void __launch_bounds__(BP_WARPS * 32 * SPLIT, SPLIT == 1 ? 5 : (SPLIT == 2 ? 2 : 1))
-bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__restrict__ f,
+bp_kernel(VolGeom g, DetGeom d, const void *__restrict__ sino, int st, const float *__restrict__ f,
           float *__restrict__ out, const double *__restrict__ d_scale, float scale_val, float kappa,
           double *__restrict__ partials, int patch_cap, int pad, int zblocks, int views_per_group)
 {
@@ -270,23 +297,16 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
         const bool staged = hp > 0;
         if (staged) {
             const int w = iu1 - iu0 + 1, h = s1 - s0 + 1;
-            const float *src = sino + (size_t)view * nv * nu;
-            for (int r = wid; r < h; r += NWARPS) {
-                const int iv = s0 + r;
-                const bool in = iv >= 0 && iv < nv;
-                for (int cc = lane; cc < w; cc += 32) {
-                    const int iu = iu0 + cc;
-                    float val = 0.f;
-                    if (in) {
-                        val = __ldg(src + (size_t)iv * nu + iu);
-                        if (!PRESCALED) {
-                            const float vl = (((float)iv - d.cv) * d.dv) * g.cols[(size_t)view * nu + iu].inv_lxy;
-                            val *= g.drho * sqrtf(1.f + vl * vl);
-                        }
-                    }
-                    patch[cc * hp + r] = val;
-                }
-            }
+            const size_t src = (size_t)view * nv * nu;
+            if (st == CBCT_STORAGE_BF16)
+                stage_patch<PRESCALED, NWARPS>(patch, static_cast<const __nv_bfloat16 *>(sino) + src, g, d, view,
+                                              iu0, s0, w, h, hp, wid, lane);
+            else if (st == CBCT_STORAGE_F16)
+                stage_patch<PRESCALED, NWARPS>(patch, static_cast<const __half *>(sino) + src, g, d, view, iu0, s0,
+                                              w, h, hp, wid, lane);
+            else
+                stage_patch<PRESCALED, NWARPS>(patch, static_cast<const float *>(sino) + src, g, d, view, iu0, s0,
+                                              w, h, hp, wid, lane);
         }
         __syncthreads();
 
@@ -384,13 +404,13 @@ bp_kernel(VolGeom g, DetGeom d, const float *__restrict__ sino, const float *__r
                             // generic path: rows outside the staged patch come from global memory
                             const int iu_e = en.cell >> 8;
                             const RayCol rce = g.cols[(size_t)view * nu + iu_e];
-                            const float *gcol = sino + (size_t)view * nv * nu + iu_e;
+                            const size_t gbase = (size_t)view * nv * nu + iu_e;
 #pragma unroll
                             for (int zc = 0; zc < BP_ZC; ++zc) {
                                 const int c = c_base + zc * 32 + lane;
                                 const float q = d.cv + ((float)c - g.cz) * en.m;
-                                sv[zc] = tent_rows<0, PRESCALED>(d, g, pcol, gcol, rce, staged, s0, s1, q, en.m,
-                                                                 en.sc);
+                                sv[zc] = tent_rows<0, PRESCALED>(d, g, pcol, sino, gbase, st, rce, staged, s0,
+                                                                 s1, q, en.m, en.sc);
                             }
                         }
                         switch (en.cell & 255) {
@@ -678,7 +698,8 @@ static cudaError_t launch_split(dim3 grid, size_t smem, cudaStream_t s, const Bp
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     bp_kernel<MODE, P, NR, ZC, SPLIT><<<grid, BP_WARPS * 32 * SPLIT, smem, s>>>(
-        L.v, L.d, L.sino, L.f, L.out, L.d_scale, L.scale_val, L.kappa, L.partials, L.cap, NR, L.zblocks, L.vpg);
+        L.v, L.d, L.sino, L.st, L.f, L.out, L.d_scale, L.scale_val, L.kappa, L.partials, L.cap, NR, L.zblocks,
+        L.vpg);
     return cudaGetLastError();
 }
 
@@ -734,6 +755,14 @@ cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, c
                         float *out, const double *d_scale, double scale_val, double kappa,
                         double *partials, int mode, int prescaled, float *split_ws, cudaStream_t s)
 {
+    return launch_back_st(v, d, sino, CBCT_STORAGE_F32, f, out, d_scale, scale_val, kappa, partials, mode,
+                          prescaled, split_ws, s);
+}
+
+cudaError_t launch_back_st(const VolGeom &v, const DetGeom &d, const void *sino, int st, const float *f,
+                           float *out, const double *d_scale, double scale_val, double kappa,
+                           double *partials, int mode, int prescaled, float *split_ws, cudaStream_t s)
+{
     const int zc = bp_zc(v), zblocks = bp_zblocks(v);
     const int groups = split_ws ? bp_view_groups(v, d) : 1;
     const int vpg = (d.n_views + groups - 1) / groups;
@@ -745,7 +774,7 @@ cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, c
     const int kid = mode == 1 ? K_BP_STEP : K_BP;
     cudaError_t e;
     const int split = bp_split_for(nr);
-    BpLaunch L{v, d, sino, f, out, d_scale, (float)scale_val, (float)kappa, partials, cap, zblocks, vpg, split};
+    BpLaunch L{v, d, sino, st, f, out, d_scale, (float)scale_val, (float)kappa, partials, cap, zblocks, vpg, split};
     launch_begin(kid, s);
     if (groups > 1) {
         BpLaunch Ls = L;

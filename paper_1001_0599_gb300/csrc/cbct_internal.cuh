@@ -1,6 +1,8 @@
 // Internal definitions shared by the libcbct translation units (sm_103a).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -190,11 +192,45 @@ void note_extra_launch();   // a second kernel inside one timed launch_begin/lau
 // mode 1: out = P vol - y (unscaled residual), partials <- sum r^2
 // mode 2: out = ds * (P vol - y) (residual pre-weighted for the transpose), partials <- sum r^2
 // mode 3: out = scale * ds * P vol (projection pre-weighted for the transpose)
+// Storage type of a volume or sinogram array (cbct_storage): values are
+// widened to FP32 on load and rounded to nearest on store; all arithmetic is
+// FP32 and reductions FP64.
+__device__ __forceinline__ float ld_st(const void *p, size_t i, int st)
+{
+    if (st == CBCT_STORAGE_BF16) return __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(p) + i));
+    if (st == CBCT_STORAGE_F16) return __half2float(__ldg(static_cast<const __half *>(p) + i));
+    return __ldg(static_cast<const float *>(p) + i);
+}
+__device__ __forceinline__ void st_st(void *p, size_t i, float v, int st)
+{
+    if (st == CBCT_STORAGE_BF16)
+        static_cast<__nv_bfloat16 *>(p)[i] = __float2bfloat16_rn(v);
+    else if (st == CBCT_STORAGE_F16)
+        static_cast<__half *>(p)[i] = __float2half_rn(v);
+    else
+        static_cast<float *>(p)[i] = v;
+}
+template <typename T> __device__ __forceinline__ float ldt(const T *p);
+template <> __device__ __forceinline__ float ldt<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldt<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float ldt<__half>(const __half *p) { return __half2float(__ldg(p)); }
+inline size_t storage_bytes(int st) { return st == CBCT_STORAGE_F32 ? 4 : 2; }
+
 int fp_grid_blocks(const DetGeom &d);                          // largest grid (workspace sizing)
 int fp_partials_count(const VolGeom &v, const DetGeom &d);      // blocks of the launch for this level
 cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
                            float *out, const double *d_scale, double *partials, int mode,
                            cudaStream_t s);
+// the same with vol, y and out stored as `st` (cbct_storage); reduced storage
+// needs the sheet variant (cudaErrorNotSupported otherwise)
+cudaError_t launch_forward_st(const VolGeom &v, const DetGeom &d, const void *vol, const void *y, void *out,
+                              int st, const double *d_scale, double *partials, int mode, cudaStream_t s);
+bool fp_supports_storage(const VolGeom &v, const DetGeom &d, int st);
+// element-wise conversion between storage types (n elements)
+cudaError_t launch_convert(const void *src, int src_st, void *dst, int dst_st, size_t n, cudaStream_t s);
 
 // transpose. mode 0: out = P^T sino; mode 1: out = f - scale P^T sino with
 // scale = *d_scale if given, else scale_val (sino pre-weighted by ds when
@@ -213,6 +249,10 @@ size_t bp_smem_bound(const VolGeom &v, const DetGeom &d);
 cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, const float *f,
                         float *out, const double *d_scale, double scale_val, double kappa,
                         double *partials, int mode, int prescaled, float *split_ws, cudaStream_t s);
+// the same with the sinogram stored as `st` (cbct_storage)
+cudaError_t launch_back_st(const VolGeom &v, const DetGeom &d, const void *sino, int st, const float *f,
+                           float *out, const double *d_scale, double scale_val, double kappa,
+                           double *partials, int mode, int prescaled, float *split_ws, cudaStream_t s);
 
 // Eq. 6 voxel-driven gradient (eq6.cu). mode 0: out = G(T); mode 1:
 // out = f - scale G(T) with scale = scale_val (* *d_scale when given)

@@ -189,10 +189,60 @@ fp_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__re
 constexpr int FS_THREADS = 128;
 constexpr int FS_J = 32;
 
+// One chunk of xy-blended sheet rows: H[jj][c] = sum of the four xy corner
+// columns weighted, for the z range [clo, chi].
+template <typename T>
+__device__ __forceinline__ void build_sheet(float *H, int hs, const T *__restrict__ vol, const int (*s_o)[FS_J],
+                                            const float (*s_w)[FS_J], int nj, int clo, int chi, int warp, int lane)
+{
+    for (int jj = warp; jj < nj; jj += FS_THREADS / 32) {
+        const int o0 = s_o[0][jj], o1 = s_o[1][jj], o2 = s_o[2][jj], o3 = s_o[3][jj];
+        const float w0 = s_w[0][jj], w1 = s_w[1][jj], w2 = s_w[2][jj], w3 = s_w[3][jj];
+        float *Hr = H + jj * hs + 2;
+        for (int c = clo + lane; c <= chi; c += 32)
+            Hr[c] = w0 * ldt(vol + o0 + c) + w1 * ldt(vol + o1 + c) + w2 * ldt(vol + o2 + c) +
+                    w3 * ldt(vol + o3 + c);
+    }
+}
+
+__device__ __forceinline__ void store_t(float *p, float v) { *p = v; }
+__device__ __forceinline__ void store_t(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void store_t(__half *p, float v) { *p = __float2half_rn(v); }
+
+// Rows of one ray line: projection (modes 0, 3) or residual (modes 1, 2) out,
+// returns the thread's sum of squared residuals
+template <int MODE, int RT, typename T>
+__device__ __forceinline__ float sheet_epilogue(const T *__restrict__ y, T *__restrict__ out, const float (&acc)[RT],
+                                                const float (&ds)[RT], float scale, size_t o_base, int tid, int nv,
+                                                int nu)
+{
+    float r2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < RT; k++) {
+        const int iv = tid + FS_THREADS * k;
+        if (iv < nv) {
+            const size_t o = o_base + (size_t)iv * nu;
+            const float p = acc[k] * ds[k];
+            if (MODE == 0) {
+                store_t(out + o, p * scale);
+            } else if (MODE == 3) {
+                store_t(out + o, p * scale * ds[k]);
+            } else {
+                const float r = p - ldt(y + o);
+                r2 += r * r;
+                store_t(out + o, (MODE == 1) ? r : r * ds[k]);
+            }
+        }
+    }
+    return r2;
+}
+
+// minimum resident blocks: 10 per SM (48 registers) for up to 3 rows per
+// thread, fewer for the taller detectors
 template <int MODE, int RT>
-__global__ void __launch_bounds__(FS_THREADS)
-fp_sheet_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__restrict__ y,
-                float *__restrict__ out, const double *__restrict__ d_scale, double *__restrict__ partials)
+__global__ void __launch_bounds__(FS_THREADS, RT <= 3 ? 10 : (RT == 4 ? 8 : 6))
+fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *__restrict__ y,
+                void *__restrict__ out, int st, const double *__restrict__ d_scale, double *__restrict__ partials)
 {
     extern __shared__ float H[];               // [FS_J][nz + 4]
     __shared__ int s_o[4][FS_J];
@@ -270,14 +320,12 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float
         }
         __syncthreads();
         const int clo = s_range[0], chi = s_range[1];
-        for (int jj = warp; jj < nj; jj += FS_THREADS / 32) {
-            const int o0 = s_o[0][jj], o1 = s_o[1][jj], o2 = s_o[2][jj], o3 = s_o[3][jj];
-            const float w0 = s_w[0][jj], w1 = s_w[1][jj], w2 = s_w[2][jj], w3 = s_w[3][jj];
-            float *Hr = H + jj * hs + 2;
-            for (int c = clo + lane; c <= chi; c += 32)
-                Hr[c] = w0 * __ldg(vol + o0 + c) + w1 * __ldg(vol + o1 + c) + w2 * __ldg(vol + o2 + c) +
-                        w3 * __ldg(vol + o3 + c);
-        }
+        if (st == CBCT_STORAGE_BF16)
+            build_sheet(H, hs, static_cast<const __nv_bfloat16 *>(vol), s_o, s_w, nj, clo, chi, warp, lane);
+        else if (st == CBCT_STORAGE_F16)
+            build_sheet(H, hs, static_cast<const __half *>(vol), s_o, s_w, nj, clo, chi, warp, lane);
+        else
+            build_sheet(H, hs, static_cast<const float *>(vol), s_o, s_w, nj, clo, chi, warp, lane);
         __syncthreads();
         // 32-row bands whose rows stay outside the volume over the whole chunk
         // (rows above the top or below the bottom for every sample) are skipped
@@ -310,25 +358,18 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float
         __syncthreads();
     }
 
-    float r2 = 0.f;
     const float scale = ((MODE == 0 || MODE == 3) && d_scale) ? (float)(*d_scale) : 1.f;
-#pragma unroll
-    for (int k = 0; k < RT; k++) {
-        const int iv = tid + FS_THREADS * k;
-        if (iv < nv) {
-            const size_t o = ((size_t)view * nv + iv) * d.nu + iu;
-            const float p = acc[k] * ds[k];
-            if (MODE == 0) {
-                out[o] = p * scale;
-            } else if (MODE == 3) {
-                out[o] = p * scale * ds[k];
-            } else {
-                const float r = p - __ldg(y + o);
-                r2 += r * r;
-                out[o] = (MODE == 1) ? r : r * ds[k];
-            }
-        }
-    }
+    const size_t o_base = (size_t)view * nv * d.nu + iu;
+    float r2;
+    if (st == CBCT_STORAGE_BF16)
+        r2 = sheet_epilogue<MODE, RT>(static_cast<const __nv_bfloat16 *>(y), static_cast<__nv_bfloat16 *>(out),
+                                      acc, ds, scale, o_base, tid, nv, d.nu);
+    else if (st == CBCT_STORAGE_F16)
+        r2 = sheet_epilogue<MODE, RT>(static_cast<const __half *>(y), static_cast<__half *>(out), acc, ds, scale,
+                                      o_base, tid, nv, d.nu);
+    else
+        r2 = sheet_epilogue<MODE, RT>(static_cast<const float *>(y), static_cast<float *>(out), acc, ds, scale,
+                                      o_base, tid, nv, d.nu);
     if (MODE == 1 || MODE == 2) {
         DF v[1] = {DF{r2, 0.f}};
         double tot[1];
@@ -390,33 +431,38 @@ int fp_partials_count(const VolGeom &v, const DetGeom &d)
 }
 
 template <int MODE, int RT>
-static cudaError_t launch_sheet_rt(const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
-                                   float *out, const double *d_scale, double *partials, cudaStream_t s)
+static cudaError_t launch_sheet_rt(const VolGeom &v, const DetGeom &d, const void *vol, const void *y,
+                                   void *out, int st, const double *d_scale, double *partials, cudaStream_t s)
 {
     const size_t smem = (size_t)FS_J * (v.nz + 4) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(fp_sheet_kernel<MODE, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    fp_sheet_kernel<MODE, RT><<<dim3(d.nu, d.n_views), FS_THREADS, smem, s>>>(v, d, vol, y, out, d_scale, partials);
+    fp_sheet_kernel<MODE, RT><<<dim3(d.nu, d.n_views), FS_THREADS, smem, s>>>(v, d, vol, y, out, st, d_scale,
+                                                                             partials);
     return cudaGetLastError();
 }
 
 template <int MODE>
-static cudaError_t launch_sheet(int rt, const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
-                                float *out, const double *d_scale, double *partials, cudaStream_t s)
+static cudaError_t launch_sheet(int rt, const VolGeom &v, const DetGeom &d, const void *vol, const void *y,
+                                void *out, int st, const double *d_scale, double *partials, cudaStream_t s)
 {
     switch (rt) {
-    case 1: return launch_sheet_rt<MODE, 1>(v, d, vol, y, out, d_scale, partials, s);
-    case 2: return launch_sheet_rt<MODE, 2>(v, d, vol, y, out, d_scale, partials, s);
-    case 3: return launch_sheet_rt<MODE, 3>(v, d, vol, y, out, d_scale, partials, s);
-    case 4: return launch_sheet_rt<MODE, 4>(v, d, vol, y, out, d_scale, partials, s);
-    default: return launch_sheet_rt<MODE, 8>(v, d, vol, y, out, d_scale, partials, s);
+    case 1: return launch_sheet_rt<MODE, 1>(v, d, vol, y, out, st, d_scale, partials, s);
+    case 2: return launch_sheet_rt<MODE, 2>(v, d, vol, y, out, st, d_scale, partials, s);
+    case 3: return launch_sheet_rt<MODE, 3>(v, d, vol, y, out, st, d_scale, partials, s);
+    case 4: return launch_sheet_rt<MODE, 4>(v, d, vol, y, out, st, d_scale, partials, s);
+    default: return launch_sheet_rt<MODE, 8>(v, d, vol, y, out, st, d_scale, partials, s);
     }
 }
 
-cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
-                           float *out, const double *d_scale, double *partials, int mode,
-                           cudaStream_t s)
+bool fp_supports_storage(const VolGeom &v, const DetGeom &d, int st)
+{
+    return st == CBCT_STORAGE_F32 || fp_sheet_rows(v, d) > 0;
+}
+
+cudaError_t launch_forward_st(const VolGeom &v, const DetGeom &d, const void *vol, const void *y, void *out,
+                              int st, const double *d_scale, double *partials, int mode, cudaStream_t s)
 {
     const int kid = (mode == 0 || mode == 3) ? K_FP : K_FP_RESID;
     const int rt = fp_sheet_rows(v, d);
@@ -424,27 +470,58 @@ cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol,
         launch_begin(kid, s);
         cudaError_t e;
         if (mode == 0)
-            e = launch_sheet<0>(rt, v, d, vol, y, out, d_scale, partials, s);
+            e = launch_sheet<0>(rt, v, d, vol, y, out, st, d_scale, partials, s);
         else if (mode == 3)
-            e = launch_sheet<3>(rt, v, d, vol, y, out, d_scale, partials, s);
+            e = launch_sheet<3>(rt, v, d, vol, y, out, st, d_scale, partials, s);
         else if (mode == 1)
-            e = launch_sheet<1>(rt, v, d, vol, y, out, d_scale, partials, s);
+            e = launch_sheet<1>(rt, v, d, vol, y, out, st, d_scale, partials, s);
         else
-            e = launch_sheet<2>(rt, v, d, vol, y, out, d_scale, partials, s);
+            e = launch_sheet<2>(rt, v, d, vol, y, out, st, d_scale, partials, s);
         launch_end(kid, s);
         return e;
     }
+    if (st != CBCT_STORAGE_F32) return cudaErrorNotSupported;
+    const float *fv = static_cast<const float *>(vol);
+    const float *fy = static_cast<const float *>(y);
+    float *fo = static_cast<float *>(out);
     const int rpl = fp_rows_per_lane(v, d);
     launch_begin(kid, s);
     if (mode == 0)
-        launch_mode<0>(v, d, vol, y, out, d_scale, partials, rpl, s);
+        launch_mode<0>(v, d, fv, fy, fo, d_scale, partials, rpl, s);
     else if (mode == 3)
-        launch_mode<3>(v, d, vol, y, out, d_scale, partials, rpl, s);
+        launch_mode<3>(v, d, fv, fy, fo, d_scale, partials, rpl, s);
     else if (mode == 1)
-        launch_mode<1>(v, d, vol, y, out, d_scale, partials, rpl, s);
+        launch_mode<1>(v, d, fv, fy, fo, d_scale, partials, rpl, s);
     else
-        launch_mode<2>(v, d, vol, y, out, d_scale, partials, rpl, s);
+        launch_mode<2>(v, d, fv, fy, fo, d_scale, partials, rpl, s);
     launch_end(kid, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const VolGeom &v, const DetGeom &d, const float *vol, const float *y,
+                           float *out, const double *d_scale, double *partials, int mode,
+                           cudaStream_t s)
+{
+    return launch_forward_st(v, d, vol, y, out, CBCT_STORAGE_F32, d_scale, partials, mode, s);
+}
+
+// ---------------------------------------------------------------------------
+// storage conversion (grid-stride, one element per thread per step)
+// ---------------------------------------------------------------------------
+__global__ void convert_kernel(const void *__restrict__ src, int src_st, void *__restrict__ dst, int dst_st,
+                               size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        st_st(dst, i, ld_st(src, i, src_st), dst_st);
+}
+
+cudaError_t launch_convert(const void *src, int src_st, void *dst, int dst_st, size_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)152 * 16);
+    launch_begin(K_MISC, s);
+    convert_kernel<<<blocks, 256, 0, s>>>(src, src_st, dst, dst_st, n);
+    launch_end(K_MISC, s);
     return cudaGetLastError();
 }
 
