@@ -237,10 +237,10 @@ __device__ __forceinline__ float sheet_epilogue(const T *__restrict__ y, T *__re
     return r2;
 }
 
-// minimum resident blocks: 10 per SM (48 registers) for up to 3 rows per
-// thread, fewer for the taller detectors
+// tall detectors (4 or 8 rows per thread) get a register budget that avoids
+// local-memory spills
 template <int MODE, int RT>
-__global__ void __launch_bounds__(FS_THREADS, RT <= 3 ? 10 : (RT == 4 ? 8 : 6))
+__global__ void __launch_bounds__(FS_THREADS, RT <= 3 ? 1 : (RT == 4 ? 8 : 6))
 fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *__restrict__ y,
                 void *__restrict__ out, int st, const double *__restrict__ d_scale, double *__restrict__ partials)
 {
