@@ -237,10 +237,11 @@ __device__ __forceinline__ float sheet_epilogue(const T *__restrict__ y, T *__re
     return r2;
 }
 
-// tall detectors (4 or 8 rows per thread) get a register budget that avoids
-// local-memory spills
+// register budgets: 56 for up to 3 rows per thread (9 blocks of 128 threads
+// per SM; deep volumes are limited by the sheet's shared memory first), and
+// enough for 4 or 8 rows to avoid local-memory spills
 template <int MODE, int RT>
-__global__ void __launch_bounds__(FS_THREADS, RT <= 3 ? 1 : (RT == 4 ? 8 : 6))
+__global__ void __launch_bounds__(FS_THREADS, RT <= 3 ? 9 : (RT == 4 ? 8 : 6))
 fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *__restrict__ y,
                 void *__restrict__ out, int st, const double *__restrict__ d_scale, double *__restrict__ partials)
 {
