@@ -213,7 +213,7 @@ cbct_status cbct_gradient_step(const cbct_geometry *geom, const float *d_r, cons
 
 /* P (Eq. 1) of a volume stored as `storage` into a sinogram stored the same
  * way (FP32 arithmetic in between). Reduced storage needs the shared-memory
- * sheet projector (nv <= 1024 and nz <= 764); otherwise CBCT_ERR_UNSUPPORTED. */
+ * sheet projector (nv <= 1024 and nz <= 760); otherwise CBCT_ERR_UNSUPPORTED. */
 cbct_status cbct_forward_project_ex(const cbct_geometry *geom, const void *d_vol, void *d_sino, int storage,
                                     void *stream);
 /* The matched transpose of a sinogram stored as `storage`, into an FP32

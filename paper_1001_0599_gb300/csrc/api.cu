@@ -516,7 +516,7 @@ extern "C" cbct_status cbct_forward_project_ex(const cbct_geometry *G, const voi
     CHECK(check_ptr(d_sino, "d_sino"));
     CHECK(check_storage(storage));
     if (!fp_supports_storage(G->lev[0].vg, G->det, storage))
-        return fail(CBCT_ERR_UNSUPPORTED, "reduced storage needs nv <= 1024 and nz <= 764");
+        return fail(CBCT_ERR_UNSUPPORTED, "reduced storage needs nv <= 1024 and nz <= 760");
     CUDA_TRY(launch_forward_st(G->lev[0].vg, G->det, d_vol, nullptr, d_sino, storage, nullptr, nullptr, 0,
                                (cudaStream_t)stream));
     return ok();
@@ -788,7 +788,7 @@ static cbct_status check_recon_params(const cbct_geometry *G, const cbct_recon_p
         if (p->gradient_mode != 0) return fail(CBCT_ERR_UNSUPPORTED, "reduced storage takes the matched gradient");
         for (int l = 0; l < p->n_levels; l++)
             if (!fp_supports_storage(G->lev[l].vg, G->det, p->storage))
-                return fail(CBCT_ERR_UNSUPPORTED, "reduced storage needs nv <= 1024 and nz <= 764");
+                return fail(CBCT_ERR_UNSUPPORTED, "reduced storage needs nv <= 1024 and nz <= 760");
     }
     CHECK(check_tv_params(&p->tv));
     replay_off.clear();

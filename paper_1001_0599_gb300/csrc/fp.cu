@@ -189,19 +189,57 @@ fp_kernel(VolGeom g, DetGeom d, const float *__restrict__ vol, const float *__re
 constexpr int FS_THREADS = 128;
 constexpr int FS_J = 32;
 
-// One chunk of xy-blended sheet rows: H[jj][c] = sum of the four xy corner
-// columns weighted, for the z range [clo, chi].
-template <typename T>
-__device__ __forceinline__ void build_sheet(float *H, int hs, const T *__restrict__ vol, const int (*s_o)[FS_J],
-                                            const float (*s_w)[FS_J], int nj, int clo, int chi, int warp, int lane)
+// Four consecutive stored values widened to FP32 (16-byte or 8-byte load;
+// the caller guarantees the alignment).
+__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p)
 {
+    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                       __uint_as_float(u.y & 0xffff0000u));
+}
+__device__ __forceinline__ float4 ld4(const __half *p)
+{
+    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Zero entries on each z side of a sheet row (the rows' interpolation reads
+// c0 in [-2, nz] and c0 + 1); four keep 16-byte alignment of the row body.
+constexpr int FS_PAD = 4;
+
+// One chunk of xy-blended sheet rows: H[jj][c] = sum of the four xy corner
+// columns weighted, for the z range [clo, chi]. With nz a multiple of 4 each
+// lane blends four consecutive z values per step (vector loads and store);
+// the range is widened to whole quads, which stay inside the volume.
+template <typename T>
+__device__ __forceinline__ void build_sheet(float *H, int hs, int nz, const T *__restrict__ vol,
+                                            const int (*s_o)[FS_J], const float (*s_w)[FS_J], int nj, int clo,
+                                            int chi, int warp, int lane)
+{
+    const bool quads = (nz & 3) == 0;
     for (int jj = warp; jj < nj; jj += FS_THREADS / 32) {
         const int o0 = s_o[0][jj], o1 = s_o[1][jj], o2 = s_o[2][jj], o3 = s_o[3][jj];
         const float w0 = s_w[0][jj], w1 = s_w[1][jj], w2 = s_w[2][jj], w3 = s_w[3][jj];
-        float *Hr = H + jj * hs + 2;
-        for (int c = clo + lane; c <= chi; c += 32)
-            Hr[c] = w0 * ldt(vol + o0 + c) + w1 * ldt(vol + o1 + c) + w2 * ldt(vol + o2 + c) +
-                    w3 * ldt(vol + o3 + c);
+        float *Hr = H + jj * hs + FS_PAD;
+        if (quads) {
+            for (int c = (clo & ~3) + 4 * lane; c <= chi; c += 128) {
+                const float4 v0 = ld4(vol + o0 + c), v1 = ld4(vol + o1 + c);
+                const float4 v2 = ld4(vol + o2 + c), v3 = ld4(vol + o3 + c);
+                float4 h;
+                h.x = w0 * v0.x + w1 * v1.x + w2 * v2.x + w3 * v3.x;
+                h.y = w0 * v0.y + w1 * v1.y + w2 * v2.y + w3 * v3.y;
+                h.z = w0 * v0.z + w1 * v1.z + w2 * v2.z + w3 * v3.z;
+                h.w = w0 * v0.w + w1 * v1.w + w2 * v2.w + w3 * v3.w;
+                *reinterpret_cast<float4 *>(Hr + c) = h;
+            }
+        } else {
+            for (int c = clo + lane; c <= chi; c += 32)
+                Hr[c] = w0 * ldt(vol + o0 + c) + w1 * ldt(vol + o1 + c) + w2 * ldt(vol + o2 + c) +
+                        w3 * ldt(vol + o3 + c);
+        }
     }
 }
 
@@ -237,15 +275,15 @@ __device__ __forceinline__ float sheet_epilogue(const T *__restrict__ y, T *__re
     return r2;
 }
 
-// register budgets: 56 for up to 3 rows per thread (9 blocks of 128 threads
+// register budgets: 64 for up to 3 rows per thread (8 blocks of 128 threads
 // per SM; deep volumes are limited by the sheet's shared memory first), and
 // enough for 4 or 8 rows to avoid local-memory spills
 template <int MODE, int RT>
-__global__ void __launch_bounds__(FS_THREADS, RT <= 3 ? 9 : (RT == 4 ? 8 : 6))
+__global__ void __launch_bounds__(FS_THREADS, RT <= 3 ? 8 : (RT == 4 ? 7 : 6))
 fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *__restrict__ y,
                 void *__restrict__ out, int st, const double *__restrict__ d_scale, double *__restrict__ partials)
 {
-    extern __shared__ float H[];               // [FS_J][nz + 4]
+    extern __shared__ float H[];               // [FS_J][nz + 2 FS_PAD]
     __shared__ int s_o[4][FS_J];
     __shared__ float s_w[4][FS_J];
     __shared__ float s_rho[FS_J];
@@ -255,7 +293,7 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int iu = blockIdx.x, view = blockIdx.y;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nv = d.nv;
-    const int hs = nz + 4;
+    const int hs = nz + 2 * FS_PAD;
     const RayCol rc = g.cols[(size_t)view * d.nu + iu];
     const float kz = d.dv * rc.inv_lxy;
 
@@ -271,7 +309,8 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *
     const float tz_max = (((float)(nv - 1) - d.cv) * kz) * g.inv_dz;
     for (int j = tid; j < FS_J; j += FS_THREADS) {
         float *Hr = H + j * hs;
-        Hr[0] = Hr[1] = Hr[nz + 2] = Hr[nz + 3] = 0.f;
+#pragma unroll
+        for (int t = 0; t < FS_PAD; ++t) Hr[t] = Hr[nz + FS_PAD + t] = 0.f;
     }
     // rows leave the volume through its top or bottom once rho is large
     int jhi = rc.jhi;
@@ -322,11 +361,11 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *
         __syncthreads();
         const int clo = s_range[0], chi = s_range[1];
         if (st == CBCT_STORAGE_BF16)
-            build_sheet(H, hs, static_cast<const __nv_bfloat16 *>(vol), s_o, s_w, nj, clo, chi, warp, lane);
+            build_sheet(H, hs, nz, static_cast<const __nv_bfloat16 *>(vol), s_o, s_w, nj, clo, chi, warp, lane);
         else if (st == CBCT_STORAGE_F16)
-            build_sheet(H, hs, static_cast<const __half *>(vol), s_o, s_w, nj, clo, chi, warp, lane);
+            build_sheet(H, hs, nz, static_cast<const __half *>(vol), s_o, s_w, nj, clo, chi, warp, lane);
         else
-            build_sheet(H, hs, static_cast<const float *>(vol), s_o, s_w, nj, clo, chi, warp, lane);
+            build_sheet(H, hs, nz, static_cast<const float *>(vol), s_o, s_w, nj, clo, chi, warp, lane);
         __syncthreads();
         // 32-row bands whose rows stay outside the volume over the whole chunk
         // (rows above the top or below the bottom for every sample) are skipped
@@ -344,7 +383,7 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *
         }
         for (int jj = 0; jj < nj; ++jj) {
             const float rho = s_rho[jj];
-            const float *Hr = H + jj * hs + 2;
+            const float *Hr = H + jj * hs + FS_PAD;
 #pragma unroll
             for (int k = 0; k < RT; k++) {
                 if (!band[k]) continue;
@@ -382,7 +421,7 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *
 // rows per thread of the sheet variant (0: use the warp variant)
 static int fp_sheet_rows(const VolGeom &v, const DetGeom &d)
 {
-    if ((size_t)FS_J * (v.nz + 4) * sizeof(float) > 96 * 1024) return 0;
+    if ((size_t)FS_J * (v.nz + 2 * FS_PAD) * sizeof(float) > 96 * 1024) return 0;
     for (int rt : {1, 2, 3, 4, 8})
         if (d.nv <= FS_THREADS * rt) return rt;
     return 0;
@@ -435,7 +474,7 @@ template <int MODE, int RT>
 static cudaError_t launch_sheet_rt(const VolGeom &v, const DetGeom &d, const void *vol, const void *y,
                                    void *out, int st, const double *d_scale, double *partials, cudaStream_t s)
 {
-    const size_t smem = (size_t)FS_J * (v.nz + 4) * sizeof(float);
+    const size_t smem = (size_t)FS_J * (v.nz + 2 * FS_PAD) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(fp_sheet_kernel<MODE, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
