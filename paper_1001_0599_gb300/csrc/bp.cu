@@ -28,7 +28,11 @@
 #endif
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 namespace cbct {
 
@@ -69,6 +73,7 @@ struct BpLaunch {
     double *partials;
     int cap, zblocks, vpg;
     int split;   // warps per column group
+    int *occ;    // non-null: report resident blocks per SM of the selected variant instead of launching
 };
 
 template <int MODE, bool P>
@@ -519,20 +524,6 @@ static int sm_count()
     return n;
 }
 
-// View groups: coarse grids have too few voxel tiles to fill the GPU, so the
-// views are split over several blocks whose raw sums a combine pass adds in
-// a fixed order.
-int bp_view_groups(const VolGeom &v, const DetGeom &d)
-{
-    const long base = (long)((v.nx + BP_TX - 1) / BP_TX) * ((v.ny + BP_TY - 1) / BP_TY) * bp_zblocks(v);
-    const long target = 4L * sm_count();
-    if (base >= target) return 1;
-    long groups = (target + base - 1) / base;
-    if (groups > d.n_views) groups = d.n_views;
-    const int per = (int)((d.n_views + groups - 1) / groups);
-    return (d.n_views + per - 1) / per;
-}
-
 size_t bp_split_floats(const VolGeom &v, const DetGeom &d)
 {
     const int gcount = bp_view_groups(v, d);
@@ -676,6 +667,61 @@ bp_combine_kernel(const float *__restrict__ part, int groups, size_t n, const fl
     }
 }
 
+// View groups. A grid's column tiles give `base` blocks, of which the GPU
+// holds `slots` at once (SMs x resident blocks of the selected variant); a
+// launch takes ceil(blocks / slots) waves. Splitting the views into groups
+// multiplies the blocks and divides each block's views, and a combine pass
+// adds the groups' raw sums in a fixed order. The group count minimises
+// waves x (views per block + per-block overhead) + the combine's cost, both
+// overheads in units of one view of one block (0.3 and 0.15, measured on the
+// paper-scale levels); one group when the tiles alone fill many waves.
+static int bp_blocks_per_sm(const VolGeom &v, const DetGeom &d)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<std::array<int, 6>, int>> cache;
+    const std::array<int, 6> key{v.nx, v.ny, v.nz, d.nu, d.nv, v.bp_cap};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const auto &kv : cache)
+            if (kv.first == key) return kv.second;
+    }
+    int occ = 0;
+    BpLaunch L{};
+    L.v = v;
+    L.d = d;
+    L.occ = &occ;
+    L.split = bp_split_for(bp_nr_variant(v, d));
+    if (bp_dispatch<3, true>(bp_zc(v), bp_nr_variant(v, d), dim3(1), dim3(1), bp_smem_bytes(v, d), 0, L) !=
+            cudaSuccess ||
+        occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache.emplace_back(key, occ);
+    return occ;
+}
+
+int bp_view_groups(const VolGeom &v, const DetGeom &d)
+{
+    const long base = (long)((v.nx + BP_TX - 1) / BP_TX) * ((v.ny + BP_TY - 1) / BP_TY) * bp_zblocks(v);
+    const long slots = (long)sm_count() * bp_blocks_per_sm(v, d);
+    if (base >= 16 * slots) return 1;
+    double best = 1e300;
+    int best_g = 1;
+    for (int g = 1; g <= d.n_views; ++g) {
+        const int per = (d.n_views + g - 1) / g;            // views per block, as the launch splits them
+        if ((d.n_views + per - 1) / per != g) continue;     // the same split as a smaller g
+        const double waves = (double)((base * g + slots - 1) / slots);
+        const double cost = waves * (per + 0.3) + (g > 1 ? 0.15 * g : 0.0);
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_g = g;
+        }
+    }
+    return best_g;
+}
+
 int bp_partials_count(const VolGeom &v, const DetGeom &d, bool split)
 {
     if (split && bp_view_groups(v, d) > 1) return BPC_BLOCKS;
@@ -697,6 +743,9 @@ static cudaError_t launch_split(dim3 grid, size_t smem, cudaStream_t s, const Bp
     e = cudaFuncSetAttribute(bp_kernel<MODE, P, NR, ZC, SPLIT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
+    if (L.occ)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(L.occ, bp_kernel<MODE, P, NR, ZC, SPLIT>,
+                                                             BP_WARPS * 32 * SPLIT, smem);
     bp_kernel<MODE, P, NR, ZC, SPLIT><<<grid, BP_WARPS * 32 * SPLIT, smem, s>>>(
         L.v, L.d, L.sino, L.st, L.f, L.out, L.d_scale, L.scale_val, L.kappa, L.partials, L.cap, NR, L.zblocks,
         L.vpg);
