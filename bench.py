@@ -310,6 +310,7 @@ def main():
     launches = cbct.cbct_launch_count() - n0 - 0
     cbct.cbct_profile_enable(False)
     prof = cbct.cbct_profile_query()
+    prof_levels = {lev: cbct.cbct_profile_query_level(lev) for lev in range(len(wl.iters))}
     sec_per_scan = job_seconds_per_scan(sum(step_ms), args.steps, world, dist, "cuda")
     total_ms = sec_per_scan * 1e3 * args.steps * world
     st = cbct.read_stats(stats)
@@ -358,7 +359,7 @@ def main():
         return 0
 
     # roofline of the dominant kernel
-    roof = roofline(prof, wl, args.steps, clocks)
+    roof = roofline(prof, prof_levels, wl)
     peaks = measured_peaks()
     workload = WORKLOAD if args.power_fine <= 0 else WORKLOAD.replace(
         "tau = 1/L (20 power iterations per level)",
@@ -581,11 +582,38 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "_source": "fallback"}
 
 
-def roofline(prof, wl, steps, clocks):
-    """Dominant kernel by device time. Projector kernels are bound by FP32
-    issue (no dense contraction, working set in L2): algorithmic work is
-    2 flops per non-zero weight of P, nnz per level from tests/golden/nnz.json;
-    peak = SMs x 128 FP32 lanes x 2 flops x max SM clock."""
+KERNEL_SOURCES = {"back_project_step": ["bp.cu"], "back_project": ["bp.cu"],
+                  "forward_residual": ["fp.cu"], "forward_project": ["fp.cu"]}
+
+
+def sources_sha1(names):
+    import hashlib
+    h = hashlib.sha1()
+    for n in names + ["cbct_internal.cuh"]:
+        with open(os.path.join(ROOT, "paper_1001_0599_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, workload, level):
+    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json),
+    or None when there is none or the kernel's sources changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            ent = json.load(fh)[f"{kernel}/{workload}/L{level}"]
+    except (OSError, KeyError, ValueError):
+        return None
+    if ent.get("sources_sha1") != sources_sha1(KERNEL_SOURCES.get(kernel, [])):
+        return None
+    return float(ent["dram_bytes_per_launch"])
+
+
+def roofline(prof, prof_levels, wl):
+    """Dominant kernel by device time, reported for its finest-level launches
+    (the bulk of its time). Projector kernels are bound by FP32 issue (no dense
+    contraction, working set in L2): algorithmic work is 2 flops per non-zero
+    weight of P, nnz per level from tests/golden/nnz.json; peak = SMs x 128
+    FP32 lanes x 2 flops x max SM clock."""
     import torch
     name, (n, ms) = max(prof.items(), key=lambda kv: kv[1][1])
     if n == 0 or ms <= 0:
@@ -599,21 +627,24 @@ def roofline(prof, wl, steps, clocks):
             nnz = json.load(fh)[wl.name]
     except (OSError, KeyError, ValueError):
         nnz = None
-    levels = len(wl.iters)
-    if name in ("back_project_step", "forward_residual", "back_project", "forward_project") and nnz:
-        # launches per reconstruction at each level (coarse -> fine)
-        flops = 0.0
-        for lev in range(levels):
-            gl = levels - 1 - lev
-            per = wl.iters[lev] if name in ("back_project_step", "forward_residual") else 20
-            flops += per * 2.0 * float(nnz[str(gl)])
-        flops *= steps
-        achieved = flops / (ms / 1e3) / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
-                "work": "2 flops per non-zero sample-voxel weight of P (nnz from the oracle's count)",
-                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
-                "avg_launch_ms": ms / n}
+    if name in KERNEL_SOURCES and nnz:
+        levels = {}
+        for lev, pl in prof_levels.items():
+            nl, msl = pl.get(name, (0, 0.0))
+            if nl and msl > 0 and str(lev) in nnz:
+                avg = msl / nl
+                levels[lev] = {"launches": nl, "avg_ms": avg,
+                               "tflops": 2.0 * float(nnz[str(lev)]) / (avg / 1e3) / 1e12}
+        if 0 not in levels:
+            return None
+        l0 = levels[0]
+        return {"kernel": name, "level": 0, "bound": "alu", "achieved": l0["tflops"], "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": l0["tflops"] / fp32_peak,
+                "traffic": measured_traffic(name, wl.name, 0),
+                "work": "2 flops per non-zero sample-voxel weight of P at the finest level "
+                        "(nnz from the oracle's count), per launch",
+                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS.json)",
+                "avg_launch_ms": l0["avg_ms"], "levels": levels}
     # TV sweeps: HBM-bound (report time only; bytes depend on the sweep count)
     return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
             "frac": None, "traffic": None, "avg_launch_ms": ms / n}

@@ -362,6 +362,9 @@ cbct_status cbct_profile_collect(void);
 int cbct_profile_kernels(void);
 const char *cbct_profile_name(int kernel);
 cbct_status cbct_profile_query(int kernel, int64_t *launches, double *total_ms);
+/* The same restricted to launches made by a reconstruction on multigrid
+ * level `level` (0 = finest), or outside any reconstruction (level -1). */
+cbct_status cbct_profile_query_level(int kernel, int level, int64_t *launches, double *total_ms);
 void cbct_profile_reset(void);
 
 #ifdef __cplusplus

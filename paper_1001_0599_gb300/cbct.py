@@ -177,6 +177,9 @@ def load() -> ctypes.CDLL:
     L.cbct_profile_name.restype = ctypes.c_char_p
     L.cbct_profile_query.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
     L.cbct_profile_query.restype = st
+    L.cbct_profile_query_level.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_double)]
+    L.cbct_profile_query_level.restype = st
     L.cbct_profile_reset.argtypes = []
     L.cbct_profile_reset.restype = None
     _lib = L
@@ -462,6 +465,18 @@ def cbct_profile_query() -> dict:
     for k in range(L.cbct_profile_kernels()):
         n, ms = ctypes.c_int64(), ctypes.c_double()
         _check(L.cbct_profile_query(k, ctypes.byref(n), ctypes.byref(ms)))
+        out[L.cbct_profile_name(k).decode()] = (int(n.value), float(ms.value))
+    return out
+
+
+def cbct_profile_query_level(level: int) -> dict:
+    """Per kernel (launches, total ms) of reconstruction launches on multigrid
+    level ``level`` (0 = finest; -1: launches outside a reconstruction)."""
+    L = load()
+    out = {}
+    for k in range(L.cbct_profile_kernels()):
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        _check(L.cbct_profile_query_level(k, level, ctypes.byref(n), ctypes.byref(ms)))
         out[L.cbct_profile_name(k).decode()] = (int(n.value), float(ms.value))
     return out
 

@@ -53,14 +53,17 @@ namespace {
 std::atomic<int64_t> g_launches{0};
 struct ProfSlot {
     int kernel;
+    int level;     // multigrid level of the launch (0 = finest), -1 outside a reconstruction
     cudaEvent_t start, stop;
 };
 bool g_prof_on = false;
 thread_local bool t_quiet = false;   // threads whose launches the profiler skips
 std::vector<ProfSlot> g_pool;
 size_t g_pool_used = 0;
-int64_t g_prof_count[K_COUNT] = {};
-double g_prof_ms[K_COUNT] = {};
+// per kernel and level slot (slot 0: outside a reconstruction, slot l + 1: level l)
+int64_t g_prof_count[K_COUNT][CBCT_MAX_LEVELS + 1] = {};
+double g_prof_ms[K_COUNT][CBCT_MAX_LEVELS + 1] = {};
+thread_local int t_level = -1;   // level the calling thread's reconstruction is on
 const char *g_names[K_COUNT] = {"forward_project", "forward_residual", "back_project",
                                 "back_project_step", "rof_persistent", "reduce",
                                 "prolongate", "fill", "misc", "eq6_gradient"};
@@ -78,6 +81,7 @@ void launch_begin(int kernel, cudaStream_t s)
     }
     ProfSlot &p = g_pool[g_pool_used];
     p.kernel = kernel;
+    p.level = t_level;
     cudaEventRecord(p.start, s);
 }
 
@@ -814,6 +818,9 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
                               void *ws, const Layout &L, cbct_recon_stats *d_stats,
                               const std::vector<int> &replay_off, bool zero_start, cudaStream_t s)
 {
+    struct LevelTag {   // profiler level tag, cleared on every exit
+        ~LevelTag() { t_level = -1; }
+    } level_tag;
     DevState *st = at<DevState>(ws, L.state);
     double *partials = at<double>(ws, L.partials);
     float *r = at<float>(ws, L.r);
@@ -837,6 +844,7 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
     for (int lev = 0; lev < Lv; lev++) {
         const int gl = Lv - 1 - lev;  // geometry level: 0 = finest
         const VolGeom &v = G->lev[gl].vg;
+        t_level = gl;
         float *f = gl == 0 ? d_vol : at<float>(ws, L.coarse[gl]);
         if (lev == 0) {
             if (Lv > 1 || zero_start) CUDA_TRY(launch_fill(f, nvox(v), 0.f, s));
@@ -957,8 +965,9 @@ extern "C" cbct_status cbct_profile_collect(void)
         CUDA_TRY(cudaEventSynchronize(p.stop));
         float ms = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&ms, p.start, p.stop));
-        g_prof_ms[p.kernel] += ms;
-        g_prof_count[p.kernel] += 1;
+        const int slot = (p.level >= 0 && p.level < CBCT_MAX_LEVELS) ? p.level + 1 : 0;
+        g_prof_ms[p.kernel][slot] += ms;
+        g_prof_count[p.kernel][slot] += 1;
     }
     g_pool_used = 0;
     return ok();
@@ -971,16 +980,31 @@ extern "C" const char *cbct_profile_name(int k) { return (k >= 0 && k < K_COUNT)
 extern "C" cbct_status cbct_profile_query(int k, int64_t *launches, double *total_ms)
 {
     if (k < 0 || k >= K_COUNT || !launches || !total_ms) return fail(CBCT_ERR_INVALID_ARG, "bad kernel id");
-    *launches = g_prof_count[k];
-    *total_ms = g_prof_ms[k];
+    *launches = 0;
+    *total_ms = 0.0;
+    for (int l = 0; l <= CBCT_MAX_LEVELS; l++) {
+        *launches += g_prof_count[k][l];
+        *total_ms += g_prof_ms[k][l];
+    }
+    return ok();
+}
+
+extern "C" cbct_status cbct_profile_query_level(int k, int level, int64_t *launches, double *total_ms)
+{
+    if (k < 0 || k >= K_COUNT || !launches || !total_ms || level < -1 || level >= CBCT_MAX_LEVELS)
+        return fail(CBCT_ERR_INVALID_ARG, "bad kernel id or level");
+    *launches = g_prof_count[k][level + 1];
+    *total_ms = g_prof_ms[k][level + 1];
     return ok();
 }
 
 extern "C" void cbct_profile_reset(void)
 {
     for (int k = 0; k < K_COUNT; k++) {
-        g_prof_count[k] = 0;
-        g_prof_ms[k] = 0.0;
+        for (int l = 0; l <= CBCT_MAX_LEVELS; l++) {
+            g_prof_count[k][l] = 0;
+            g_prof_ms[k][l] = 0.0;
+        }
     }
     g_pool_used = 0;
 }
