@@ -46,6 +46,9 @@ CASES = {
                                   sad=150.0, sdd=230.0),
     "tall": synthetic.Workload("tall", 16, 16, 130, 2.0, 2.0, 0.8, 30, 140, 1.5, 1.2, 4, sad=400.0,
                                sdd=600.0),
+    # exactly 1024 detector rows: the tallest detector of the sheet projector (8 rows per thread)
+    "rows_1024": synthetic.Workload("rows_1024", 8, 10, 180, 2.0, 2.0, 0.45, 11, 1024, 2.2, 0.33, 3,
+                                    sad=300.0, sdd=450.0),
     # more than 1024 detector rows: exercises the warp-per-column projector variant
     "very_tall": synthetic.Workload("very_tall", 10, 9, 300, 2.0, 2.0, 0.3, 9, 1100, 2.5, 0.35, 2,
                                     sad=300.0, sdd=450.0),
