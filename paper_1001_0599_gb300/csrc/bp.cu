@@ -228,6 +228,34 @@ __device__ __forceinline__ void add_corners(float (&acc)[BP_G][BP_G][ZC], float 
 // patches leave room for few blocks per SM). With a view split (MODE 3) block z
 // index = z block + zblocks * view group, and the block adds only its group's
 // views and writes the raw sums to out + group * N_vox.
+// Add one sample's z sums to the group's columns its cell touches: a
+// warp-uniform switch over the 25 cells of the group and its one-voxel rim.
+template <int ZC>
+__device__ __forceinline__ void add_entry(float (&acc)[BP_G][BP_G][ZC], const SampleEntry &en, const float (&sv)[ZC])
+{
+    switch (en.cell & 255) {
+#define CBCT_CORNER(RA, RB)                                                                         \
+    case ((RA) + 1) * (BP_G + 1) + ((RB) + 1):                                                      \
+        add_corners<RA, RB, ZC>(acc, en.w00, en.w01, en.w10, en.w11, sv);                           \
+        break;
+#define CBCT_CORNER_ROW(RA)                                                                         \
+    CBCT_CORNER(RA, -1) CBCT_CORNER(RA, 0) CBCT_CORNER(RA, 1) CBCT_CORNER(RA, 2) CBCT_CORNER(RA, 3)
+        CBCT_CORNER_ROW(-1)
+        CBCT_CORNER_ROW(0)
+        CBCT_CORNER_ROW(1)
+        CBCT_CORNER_ROW(2)
+        CBCT_CORNER_ROW(3)
+#undef CBCT_CORNER_ROW
+#undef CBCT_CORNER
+    default:
+        break;
+    }
+}
+
+#ifndef CBCT_BP_DUAL
+#define CBCT_BP_DUAL 1
+#endif
+
 template <int MODE, bool PRESCALED, int NR, int ZC, int SPLIT>
 __global__ void __launch_bounds__(BP_WARPS * 32 * SPLIT, SPLIT == 1 ? 5 : (SPLIT == 2 ? 2 : 1))
 bp_kernel(VolGeom g, DetGeom d, const void *__restrict__ sino, int st, const float *__restrict__ f,
@@ -394,7 +422,29 @@ bp_kernel(VolGeom g, DetGeom d, const void *__restrict__ sino, int st, const flo
                     __syncwarp();
                     const int nwin = min(NENT * SPLIT, total - b0);
                     const int nb = (nwin - part + SPLIT - 1) / SPLIT;
-                    for (int e = 0; e < nb; ++e) {
+                    int e = 0;
+                    if (CBCT_BP_DUAL && SPLIT == 1 && NR > 0 && staged) {
+                        // two samples per step: their tents are independent, which
+                        // doubles the arithmetic chains in flight (entries outside
+                        // the group still read inside the patch and are dropped).
+                        // Short tents only: the long-tent variants (several warps per
+                        // group) measured slower this way.
+                        for (; e + 1 < nb; e += 2) {
+                            const SampleEntry ea = ent[e], eb = ent[e + 1];
+                            float sa[BP_ZC], sb[BP_ZC];
+#pragma unroll
+                            for (int zc = 0; zc < BP_ZC; ++zc) {
+                                const float cz = (float)(c_base + zc * 32 + lane) - g.cz;
+                                sa[zc] = tent_rows_staged<NR>(patch + ea.col, staged, s0, s1, d.cv + cz * ea.m, ea.m,
+                                                              ea.sc);
+                                sb[zc] = tent_rows_staged<NR>(patch + eb.col, staged, s0, s1, d.cv + cz * eb.m, eb.m,
+                                                              eb.sc);
+                            }
+                            if (ea.cell >= 0) add_entry<ZC>(acc, ea, sa);
+                            if (eb.cell >= 0) add_entry<ZC>(acc, eb, sb);
+                        }
+                    }
+                    for (; e < nb; ++e) {
                         const SampleEntry en = ent[e];
                         if (en.cell < 0) continue;  // uniform
                         const float *pcol = patch + en.col;
@@ -418,23 +468,7 @@ bp_kernel(VolGeom g, DetGeom d, const void *__restrict__ sino, int st, const flo
                                                                  s1, q, en.m, en.sc);
                             }
                         }
-                        switch (en.cell & 255) {
-#define CBCT_CORNER(RA, RB)                                                                         \
-    case ((RA) + 1) * (BP_G + 1) + ((RB) + 1):                                                      \
-        add_corners<RA, RB, ZC>(acc, en.w00, en.w01, en.w10, en.w11, sv);                           \
-        break;
-#define CBCT_CORNER_ROW(RA)                                                                         \
-    CBCT_CORNER(RA, -1) CBCT_CORNER(RA, 0) CBCT_CORNER(RA, 1) CBCT_CORNER(RA, 2) CBCT_CORNER(RA, 3)
-                            CBCT_CORNER_ROW(-1)
-                            CBCT_CORNER_ROW(0)
-                            CBCT_CORNER_ROW(1)
-                            CBCT_CORNER_ROW(2)
-                            CBCT_CORNER_ROW(3)
-#undef CBCT_CORNER_ROW
-#undef CBCT_CORNER
-                        default:
-                            break;
-                        }
+                        add_entry<ZC>(acc, en, sv);
                     }
                     __syncwarp();
                 }
