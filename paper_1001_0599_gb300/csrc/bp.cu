@@ -252,9 +252,11 @@ __device__ __forceinline__ void add_entry(float (&acc)[BP_G][BP_G][ZC], const Sa
     }
 }
 
-#ifndef CBCT_BP_DUAL
-#define CBCT_BP_DUAL 1
+// samples taken together in the transpose's main loop (short tents)
+#ifndef CBCT_BP_STEP
+#define CBCT_BP_STEP 2
 #endif
+constexpr int BP_STEP = CBCT_BP_STEP;
 
 template <int MODE, bool PRESCALED, int NR, int ZC, int SPLIT>
 __global__ void __launch_bounds__(BP_WARPS * 32 * SPLIT, SPLIT == 1 ? 5 : (SPLIT == 2 ? 2 : 1))
@@ -423,25 +425,28 @@ bp_kernel(VolGeom g, DetGeom d, const void *__restrict__ sino, int st, const flo
                     const int nwin = min(NENT * SPLIT, total - b0);
                     const int nb = (nwin - part + SPLIT - 1) / SPLIT;
                     int e = 0;
-                    if (CBCT_BP_DUAL && SPLIT == 1 && NR > 0 && staged) {
-                        // two samples per step: their tents are independent, which
-                        // doubles the arithmetic chains in flight (entries outside
+                    if (BP_STEP > 1 && SPLIT == 1 && NR > 0 && staged) {
+                        // BP_STEP samples per step: their tents are independent, which
+                        // multiplies the arithmetic chains in flight (entries outside
                         // the group still read inside the patch and are dropped).
                         // Short tents only: the long-tent variants (several warps per
                         // group) measured slower this way.
-                        for (; e + 1 < nb; e += 2) {
-                            const SampleEntry ea = ent[e], eb = ent[e + 1];
-                            float sa[BP_ZC], sb[BP_ZC];
+                        for (; e + BP_STEP - 1 < nb; e += BP_STEP) {
+                            SampleEntry es[BP_STEP];
+                            float sv[BP_STEP][BP_ZC];
+#pragma unroll
+                            for (int u = 0; u < BP_STEP; ++u) es[u] = ent[e + u];
 #pragma unroll
                             for (int zc = 0; zc < BP_ZC; ++zc) {
                                 const float cz = (float)(c_base + zc * 32 + lane) - g.cz;
-                                sa[zc] = tent_rows_staged<NR>(patch + ea.col, staged, s0, s1, d.cv + cz * ea.m, ea.m,
-                                                              ea.sc);
-                                sb[zc] = tent_rows_staged<NR>(patch + eb.col, staged, s0, s1, d.cv + cz * eb.m, eb.m,
-                                                              eb.sc);
+#pragma unroll
+                                for (int u = 0; u < BP_STEP; ++u)
+                                    sv[u][zc] = tent_rows_staged<NR>(patch + es[u].col, staged, s0, s1,
+                                                                     d.cv + cz * es[u].m, es[u].m, es[u].sc);
                             }
-                            if (ea.cell >= 0) add_entry<ZC>(acc, ea, sa);
-                            if (eb.cell >= 0) add_entry<ZC>(acc, eb, sb);
+#pragma unroll
+                            for (int u = 0; u < BP_STEP; ++u)
+                                if (es[u].cell >= 0) add_entry<ZC>(acc, es[u], sv[u]);
                         }
                     }
                     for (; e < nb; ++e) {

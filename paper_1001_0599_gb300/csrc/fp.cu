@@ -381,6 +381,7 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *
                 band[k] = !(zhi < -1.f || zlo >= (float)nz);
             }
         }
+#pragma unroll 4
         for (int jj = 0; jj < nj; ++jj) {
             const float rho = s_rho[jj];
             const float *Hr = H + jj * hs + FS_PAD;
