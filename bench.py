@@ -360,6 +360,7 @@ def main():
 
     # roofline of the dominant kernel
     roof = roofline(prof, prof_levels, wl)
+    bandwidth = projector_bandwidth(prof_levels, wl)
     peaks = measured_peaks()
     workload = WORKLOAD if args.power_fine <= 0 else WORKLOAD.replace(
         "tau = 1/L (20 power iterations per level)",
@@ -383,6 +384,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "reductions": "FP64 across blocks, compensated FP32 within"},
             "clocks": clocks, "gpu_launches": int(launches), "roofline": roof,
+            "projector_bandwidth": bandwidth,
             "e2e": e2e,
             "kernels": {k: {"launches": n // max(args.steps, 1), "ms_per_step": ms / max(args.steps, 1)}
                         for k, (n, ms) in prof.items() if n},
@@ -606,6 +608,39 @@ def measured_traffic(kernel, workload, level):
     if ent.get("sources_sha1") != sources_sha1(KERNEL_SOURCES.get(kernel, [])):
         return None
     return float(ent["dram_bytes_per_launch"])
+
+
+def projector_bandwidth(prof_levels, wl):
+    """Projector and transpose at the finest level against HBM: algorithmic
+    bytes per call (forward + residual: f, y read, r written; transpose step:
+    r, f read, g written) over the measured call time, as a fraction of the
+    measured copy bandwidth; DRAM bytes from the ncu capture over the same
+    time; and gathered bytes, 32 B (8 FP32 corner values) per trilinear sample,
+    nnz / 8 samples per call."""
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "nnz.json")) as fh:
+            nnz0 = float(json.load(fh)[wl.name]["0"])
+    except (OSError, KeyError, ValueError):
+        return None
+    nvox = wl.nx * wl.ny * wl.nz
+    nray = wl.n_views * wl.nv * wl.nu
+    out = {}
+    for name, algo in (("forward_residual", 4 * (nvox + 2 * nray)), ("back_project_step", 4 * (nray + 2 * nvox))):
+        n, ms = prof_levels.get(0, {}).get(name, (0, 0.0))
+        if not n:
+            continue
+        t = ms / n / 1e3
+        traffic = measured_traffic(name, wl.name, 0)
+        out[name] = {"algorithmic_bytes": algo, "algorithmic_gbs": algo / t / 1e9, "hbm_peak_gbs": hbm,
+                     "frac_of_hbm": algo / t / 1e9 / hbm,
+                     "dram_gbs": (traffic / t / 1e9) if traffic else None,
+                     "gathered_gbs": 32.0 * nnz0 / 8.0 / t / 1e9, "samples_per_s": nnz0 / 8.0 / t,
+                     "avg_ms": t * 1e3}
+    out["note"] = ("not HBM-bound: the per-call working set sits in L2 and both kernels are bound by "
+                   "instruction issue; see roofline")
+    return out
 
 
 def roofline(prof, prof_levels, wl):

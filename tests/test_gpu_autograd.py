@@ -149,3 +149,42 @@ def test_unrolled_data_steps_checkpointed_match_oracle_recursion(ag, orc):
     assert rel_l2(fK, f) < 1e-4
     assert rel_l2(gyt, gy) < 1e-4
     assert rel_l2(gft, v) < 1e-4
+
+
+def test_central_differences_with_tv_term(ag, c4):
+    # the 128^3 / 60-view workload's loss: data term plus TV, 1/2 |P f - y|^2 +
+    # mu N_vox E1(f) with E1 smoothed by eps = 1e-3; the TV part is not
+    # quadratic, so the step is small (truncation O(h^2 / |grad f|^2) ~ 1e-3)
+    import torch
+    wl, g, truth, y = c4
+    rng = np.random.default_rng(15)
+    f0 = np.asarray(0.8 * truth + 0.002 * rng.standard_normal(truth.shape), dtype=np.float32)
+    f = torch.from_numpy(f0).cuda().requires_grad_(True)
+    yd = dev(y).double()
+    eps, mu = 1e-3, 50.0
+    nvox = f.numel()
+
+    def loss(v):
+        return 0.5 * ((ag.forward_project(g, v).double() - yd) ** 2).sum() + mu * nvox * ag.tv_energy(g, v, eps)
+
+    loss(f).backward()
+    grad = host(f.grad)
+    idx = rng.integers(0, nvox, 64)
+    h = 1e-4
+    num = []
+    with torch.no_grad():
+        base = f.detach().clone()
+        flat = base.view(-1)
+        for j in idx:
+            old = float(flat[j])
+            up = float(np.float32(old + h))
+            dn = float(np.float32(old - h))
+            flat[j] = up
+            lp = float(loss(base))
+            flat[j] = dn
+            lm = float(loss(base))
+            flat[j] = old
+            num.append((lp - lm) / (up - dn))
+    num = np.array(num)
+    got = grad.ravel()[idx]
+    assert rel_l2(got, num) < 5e-3

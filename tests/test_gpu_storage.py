@@ -144,3 +144,32 @@ def test_multigrid_recon_with_storage_runs_all_levels(lib, orc):
     vol = torch.zeros(g.vol_shape, device="cuda")
     lib.cbct_reconstruct(g, dev(y), vol, params, ws, lib.stats_buffer())
     assert rel_l2(host(vol), ref.f) < 10 * TOL_RECON
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("storage", ["bf16", "fp16"])
+def test_lowdose_sampled_parity_with_storage(lib, orc, storage):
+    """Full 360-view 256^3 low-dose workload with stored volume and sinogram:
+    P on 300 sampled rays against the oracle's rays through the same rounded
+    volume (half an ulp of the stored type plus 1e-5), and the storage error
+    against the unrounded volume stated as a bound."""
+    import torch
+    from paper_1001_0599_gb300 import synthetic
+    wl = synthetic.workload("lowdose")
+    g = lib.geometry_from_workload(wl)
+    og = orc.Geometry.from_workload(wl)
+    truth = synthetic.voxelise(synthetic.make_phantom(wl), wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz)
+    fq = orc.round_storage(truth, storage)
+    vol = torch.from_numpy(truth.astype(np.float32)).cuda().to(_tdtype(storage))
+    out = torch.empty(og.sino_shape, dtype=_tdtype(storage), device="cuda")
+    lib.cbct_forward_project_ex(g, vol, out)
+    ph = host(out.float())
+    rng = np.random.default_rng(17)
+    n = 300
+    view, iv, iu = rng.integers(0, og.n_views, n), rng.integers(0, og.nv, n), rng.integers(0, og.nu, n)
+    ref = orc.forward_rays(og, fq, view, iv, iu)
+    got = ph[view, iv, iu]
+    bound = 0.5 * _ulp(ref, storage) + TOL_CALL * np.abs(ref).max()
+    assert np.all(np.abs(got - ref) <= bound)
+    full = orc.forward_rays(og, truth, view, iv, iu)
+    assert rel_l2(got, full) < 2.0 ** -(BITS[storage][0] - 1)
