@@ -49,6 +49,9 @@ CASES = {
     # exactly 1024 detector rows: the tallest detector of the sheet projector (8 rows per thread)
     "rows_1024": synthetic.Workload("rows_1024", 8, 10, 180, 2.0, 2.0, 0.45, 11, 1024, 2.2, 0.33, 3,
                                     sad=300.0, sdd=450.0),
+    # z tents over 17-20 detector rows: the transpose's long-tent (interval-sum) variant
+    "long_tent": synthetic.Workload("long_tent", 24, 24, 40, 2.0, 2.0, 2.0, 48, 160, 1.5, 0.4, 5,
+                                    sad=500.0, sdd=750.0),
     # more than 1024 detector rows: exercises the warp-per-column projector variant
     "very_tall": synthetic.Workload("very_tall", 10, 9, 300, 2.0, 2.0, 0.3, 9, 1100, 2.5, 0.35, 2,
                                     sad=300.0, sdd=450.0),
