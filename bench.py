@@ -128,7 +128,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
-def oracle_sample(wl, y):
+def oracle_sample(wl, y, power_fine: int = 4):
     """Seconds per reconstruction of the FP64 oracle, from a bounded sample:
     P and P^T over a subset of views and one ROF solve at every multigrid
     level, scaled by the schedule's operation counts."""
@@ -156,7 +156,7 @@ def oracle_sample(wl, y):
         scale = gl.n_views / nsub
         tp, tpt, trof = (t1 - t0) * scale, (t2 - t1) * scale, t3 - t2
         n_fbs = wl.iters[lev]
-        n_pow = 20
+        n_pow = 20 if lev == 0 or power_fine <= 0 else power_fine
         t_total += n_fbs * (tp + tpt + trof) + n_pow * (tp + tpt)
         parts.append(f"level {lev}: P,P^T on {nsub}/{gl.n_views} views x{scale:.0f}, one ROF solve")
     return t_total, "; ".join(parts)
@@ -191,6 +191,42 @@ def oracle_sample_warm(wl):
     orc.back_project(sub, orc.forward_project(sub, np.ones(g.vol_shape)))
 
 
+def workload_description(args):
+    """(workload text, metric name) of a run's configuration."""
+    workload = WORKLOAD if args.power_fine <= 0 else WORKLOAD.replace(
+        "tau = 1/L (20 power iterations per level)",
+        f"tau = 1/L (20 power iterations on the coarsest level, {args.power_fine} per finer level "
+        f"warm-started from the prolongated eigenvector)")
+    if args.gradient == "eq6":
+        workload += "; Step 1 gradient from the paper's closed form (Eq. 6) instead of the matched transpose"
+    metric = METRIC
+    if args.workload == "lowdose":
+        workload = workload.replace("paper-scale: 256x256x128 voxels", "low-dose: 256x256x256 voxels").replace(
+            "40 views/360 deg", "360 views/360 deg").replace("Poisson 5e4", "Poisson 1e4")
+        metric = "recon sec at 256^3 x 360 views (low-dose workload)"
+    if args.storage != "f32":
+        workload += (f"; measured sinogram, residual and the projector's volume copy stored as {args.storage} "
+                     "(FP32 arithmetic, FP64 sums)")
+    return workload, metric
+
+
+def cpu_baseline_subprocess():
+    """The oracle's bounded sample timed in a fresh process (this one holds a
+    CUDA context and PyTorch's thread pools), exactly as the reference arm
+    times it: one untimed warm-up projection, then the sample."""
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "LOCAL_RANK", "WORLD_SIZE", "MASTER_ADDR", "MASTER_PORT")}
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, env=env, cwd=ROOT)
+    lines = [l for l in res.stdout.splitlines() if l.startswith("{")]
+    if res.returncode != 0 or not lines:
+        return {"value": None, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+                "sample": "failed: " + (res.stderr.strip().splitlines() or ["no output"])[-1]}
+    ref = json.loads(lines[-1])["cpu_baseline"]
+    ref["sample"] += " (scaled to one reconstruction; timed in a separate process)"
+    return ref
+
+
 def cpu_cores():
     try:
         return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count())
@@ -206,17 +242,18 @@ def run_reference(args, rank, world):
     orc.build()
     wl = synthetic.workload("paper")
     _, y = synthetic.make_problem(wl)
+    oracle_sample_warm(wl)
     times = []
     sample = ""
     for i in range(args.warmup + args.steps):
-        t, sample = oracle_sample(wl, y)
+        t, sample = oracle_sample(wl, y, args.power_fine)
         if i >= args.warmup:
             times.append(t)
     v = statistics.mean(times)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": workload_description(args)[1], "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "host cores (OpenMP)"},
+            "config": {"workload": workload_description(args)[0], "parallelism": "host cores (OpenMP)"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -362,20 +399,7 @@ def main():
     roof = roofline(prof, prof_levels, wl)
     bandwidth = projector_bandwidth(prof_levels, wl)
     peaks = measured_peaks()
-    workload = WORKLOAD if args.power_fine <= 0 else WORKLOAD.replace(
-        "tau = 1/L (20 power iterations per level)",
-        f"tau = 1/L (20 power iterations on the coarsest level, {args.power_fine} per finer level "
-        f"warm-started from the prolongated eigenvector)")
-    if args.gradient == "eq6":
-        workload += "; Step 1 gradient from the paper's closed form (Eq. 6) instead of the matched transpose"
-    metric = METRIC
-    if args.workload == "lowdose":
-        workload = workload.replace("paper-scale: 256x256x128 voxels", "low-dose: 256x256x256 voxels").replace(
-            "40 views/360 deg", "360 views/360 deg").replace("Poisson 5e4", "Poisson 1e4")
-        metric = "recon sec at 256^3 x 360 views (low-dose workload)"
-    if args.storage != "f32":
-        workload += (f"; measured sinogram, residual and the projector's volume copy stored as {args.storage} "
-                     "(FP32 arithmetic, FP64 sums)")
+    workload, metric = workload_description(args)
     line = {"metric": metric, "value": sec_per_scan, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32 ({args.storage} storage)",
@@ -393,12 +417,7 @@ def main():
             "paper_context": PAPER_CONTEXT,
             "peaks_source": peaks.get("_source")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import oracle as orc
-        orc.build()
-        oracle_sample_warm(wl)
-        v, sample = oracle_sample(wl, y)
-        line["cpu_baseline"] = {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
-                                "sample": sample + " (scaled to one reconstruction)"}
+        line["cpu_baseline"] = cpu_baseline_subprocess()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
