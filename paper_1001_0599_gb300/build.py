@@ -53,7 +53,8 @@ def _compile(unit, verbose: bool, extra) -> str:
     path = os.path.join(CSRC, src)
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(path), _deps()):
         return obj
-    cmd = [nvcc(), *_flags(tuple(extra) + tuple(defs)), "-c", path, "-o", obj + ".tmp"]
+    tmp = obj + f".tmp{os.getpid()}"   # concurrent builds (one per rank) never share a temporary
+    cmd = [nvcc(), *_flags(tuple(extra) + tuple(defs)), "-c", path, "-o", tmp]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,7 +62,7 @@ def _compile(unit, verbose: bool, extra) -> str:
         raise RuntimeError(f"nvcc failed on {src}:\n{res.stdout}\n{res.stderr}")
     if verbose and res.stderr:
         sys.stderr.write(res.stderr)
-    os.replace(obj + ".tmp", obj)
+    os.replace(tmp, obj)
     return obj
 
 
