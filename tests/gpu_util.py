@@ -52,6 +52,13 @@ CASES = {
     # z tents over 17-20 detector rows: the transpose's long-tent (interval-sum) variant
     "long_tent": synthetic.Workload("long_tent", 24, 24, 40, 2.0, 2.0, 2.0, 48, 160, 1.5, 0.4, 5,
                                     sad=500.0, sdd=750.0),
+    # a fine, wide detector: the transpose's staged patch exceeds shared memory and
+    # rows are read from global memory (unstaged path)
+    "unstaged": synthetic.Workload("unstaged", 16, 16, 12, 2.0, 2.0, 2.0, 1200, 40, 0.04, 0.5, 3,
+                                   sad=300.0, sdd=450.0),
+    # a single voxel
+    "single_voxel": synthetic.Workload("single_voxel", 1, 1, 1, 2.0, 2.0, 2.0, 9, 7, 1.0, 1.0, 3,
+                                       sad=100.0, sdd=150.0),
     # more than 1024 detector rows: exercises the warp-per-column projector variant
     "very_tall": synthetic.Workload("very_tall", 10, 9, 300, 2.0, 2.0, 0.3, 9, 1100, 2.5, 0.35, 2,
                                     sad=300.0, sdd=450.0),
