@@ -355,6 +355,19 @@ def main():
     recon = vol.cpu().numpy().astype(np.float64)
     rel_err = float(np.linalg.norm(recon - truth) / np.linalg.norm(truth))
     corr = float(np.corrcoef(recon.ravel(), truth.ravel())[0, 1])
+    storage_error = None
+    if args.storage != "f32" and args.mode == "recon":
+        # the same reconstruction with FP32 storage, untimed: the reduced
+        # storage's effect on the result
+        p32 = cbct.make_recon_params(wl.lam, wl.iters, tv, power_iters=20, clamp=True,
+                                     power_iters_fine=args.power_fine, gradient=args.gradient)
+        ws32 = cbct.workspace(cbct.cbct_workspace_size(g, p32))
+        vol32 = torch.zeros(g.vol_shape, device="cuda")
+        cbct.cbct_reconstruct(g, d_y, vol32, p32, ws32)
+        r32 = vol32.cpu().numpy().astype(np.float64)
+        storage_error = {"rel_l2_vs_f32_storage": float(np.linalg.norm(recon - r32) / np.linalg.norm(r32)),
+                         "f32_rel_error_vs_phantom": float(np.linalg.norm(r32 - truth) / np.linalg.norm(truth))}
+        del ws32, vol32
 
     # end to end through the host-buffer entry point (pinned buffers)
     e2e = None
@@ -413,6 +426,7 @@ def main():
             "e2e": e2e,
             "kernels": {k: {"launches": n // max(args.steps, 1), "ms_per_step": ms / max(args.steps, 1)}
                         for k, (n, ms) in prof.items() if n},
+            "storage_error": storage_error,
             "quality": {"rel_error_vs_phantom": rel_err, "correlation": corr, "flags": int(st.flags),
                         "status": int(st.status), "taus": [float(st.tau[i]) for i in range(3)]},
             "paper_context": PAPER_CONTEXT,
