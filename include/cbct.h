@@ -248,6 +248,14 @@ cbct_status cbct_tv_denoise(const cbct_geometry *geom, const float *d_g, float *
                             double lambda, double tau, const cbct_tv_params *params,
                             void *d_ws, size_t ws_bytes, cbct_tv_stats *d_stats, void *stream);
 
+/* Failure-detection check (no counterpart in the paper): runs the ROF
+ * kernel's first grid barrier with no block ever completing it, so every
+ * block's bounded wait expires (after 2 s) and the kernel returns. Once the
+ * stream has synchronised, d_stats->status (device) reads CBCT_ERR_TIMEOUT,
+ * and the context is still usable. Uses the workspace's g and d volumes. */
+cbct_status cbct_check_barrier_timeout(const cbct_geometry *geom, void *d_ws, size_t ws_bytes,
+                                       cbct_tv_stats *d_stats, void *stream);
+
 /* ---- multigrid and step size ------------------------------------------ */
 
 /* Cell-centred trilinear prolongation (clamp to edge) from a

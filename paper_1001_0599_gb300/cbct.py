@@ -140,6 +140,8 @@ def load() -> ctypes.CDLL:
     L.cbct_tv_trial.restype = st
     L.cbct_tv_denoise.argtypes = [_P, _P, _P, d, d, ctypes.POINTER(TvParams), _P, ctypes.c_size_t, _P, _P]
     L.cbct_tv_denoise.restype = st
+    L.cbct_check_barrier_timeout.argtypes = [_P, _P, ctypes.c_size_t, _P, _P]
+    L.cbct_check_barrier_timeout.restype = st
     L.cbct_prolongate.argtypes = [ctypes.c_int] * 3 + [_P, _P, _P]
     L.cbct_prolongate.restype = st
     L.cbct_power_lipschitz.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_size_t, _P]
@@ -346,6 +348,13 @@ def cbct_tv_denoise(geom: Geometry, g, f, lam, tau, params: TvParams, ws, stats=
     _check(load().cbct_tv_denoise(geom.handle, _f32(g, "g"), _f32(f, "f"), lam, tau, ctypes.byref(params),
                                   _dev(ws, "ws"), ws.numel() * ws.element_size(),
                                   _dev(stats, "stats"), _stream(stream)))
+
+
+def cbct_check_barrier_timeout(geom: Geometry, ws, stats, stream=None) -> None:
+    """Make the ROF kernel's bounded barrier wait expire (failure detection);
+    ``stats`` (a TvStats device buffer) then reports CBCT_ERR_TIMEOUT."""
+    _check(load().cbct_check_barrier_timeout(geom.handle, _dev(ws, "ws"), ws.numel() * ws.element_size(),
+                                             _dev(stats, "stats"), _stream(stream)))
 
 
 def cbct_prolongate(coarse, fine, stream=None) -> None:

@@ -637,6 +637,32 @@ extern "C" cbct_status cbct_tv_energy_grad(const cbct_geometry *G, const float *
     return ok();
 }
 
+extern "C" cbct_status cbct_check_barrier_timeout(const cbct_geometry *G, void *ws, size_t ws_bytes,
+                                                  cbct_tv_stats *d_stats, void *stream)
+{
+    CHECK(check_geom(G));
+    if (!d_stats) return fail(CBCT_ERR_INVALID_ARG, "d_stats is NULL");
+    CHECK(check_ws(G, nullptr, ws, ws_bytes, false));
+    const Layout L = layout(G, nullptr, false);
+    cudaStream_t s = (cudaStream_t)stream;
+    const VolGeom &v = G->lev[0].vg;
+    float *g = at<float>(ws, L.g), *d = at<float>(ws, L.d);
+    CUDA_TRY(launch_fill(g, nvox(v), 0.f, s));
+    RofArgs a = rof_base(G, 0, ws, L);
+    a.g = g;
+    a.cur = g;
+    a.d = d;
+    a.lambda = 1.0;
+    a.tau = 1.0;
+    a.eps = 1e-3;
+    a.mode = 1;
+    a.out = at<double>(ws, L.partials);   // the energies never arrive; any scratch will do
+    a.tv_stats = d_stats;
+    a.withhold_arrival = 1;
+    CUDA_TRY(launch_rof(a, s));
+    return ok();
+}
+
 extern "C" cbct_status cbct_tv_trial(const cbct_geometry *G, const float *d_f, const float *d_d, const float *d_g,
                                      double s, double lambda, double tau, double eps_tv, double *d_out, void *ws,
                                      size_t ws_bytes, void *stream)

@@ -297,6 +297,8 @@ struct RofArgs {
     const float *dir;     // mode 2: direction
     const float *cur;     // modes 1, 2: iterate
     int level;
+    int withhold_arrival; // failure-detection check: no block ever completes the barrier, so
+                          // every bounded wait expires and the kernel reports a timeout
 };
 int rof_grid_blocks();
 cudaError_t launch_rof(const RofArgs &a, cudaStream_t s);

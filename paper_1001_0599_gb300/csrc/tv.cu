@@ -472,6 +472,11 @@ cudaError_t launch_rof(const RofArgs &a, cudaStream_t s)
     if (blocks < 1) blocks = 1;
     cudaError_t e = cudaMemsetAsync(&a.st->bar, 0, sizeof(GridBarrier), s);
     if (e != cudaSuccess) return e;
+    if (a.withhold_arrival) {
+        // arrivals start far above the grid size, so none is ever the last
+        e = cudaMemsetAsync(&a.st->bar.count, 0x7f, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+    }
     RofArgs args = a;
     void *params[] = {&args};
     launch_begin(K_ROF, s);

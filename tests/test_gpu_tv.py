@@ -112,3 +112,34 @@ def test_power_iteration_matches_oracle(lib, orc, level):
     lib.cbct_power_lipschitz(geom, level, 20, out, ws)
     ref = orc.power_lipschitz(og.coarse(2 ** level) if level else og, 20)
     assert float(out.item()) == pytest.approx(ref, rel=1e-5)
+
+
+def test_barrier_timeout_is_reported_and_context_survives(lib, orc):
+    # failure detection on the GPU without a fault: the ROF kernel's grid
+    # barrier is never completed, every block's bounded wait (2 s) expires, the
+    # kernel returns and the statistics report CBCT_ERR_TIMEOUT; afterwards the
+    # same workspace serves a normal solve that matches the oracle
+    import time
+
+    import torch
+    wl, geom, og = geometries("small")
+    ws = lib.workspace(lib.cbct_workspace_size(geom))
+    st = lib.stats_buffer(lib.TvStats)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lib.cbct_check_barrier_timeout(geom, ws, st)
+    torch.cuda.synchronize()
+    waited = time.perf_counter() - t0
+    assert lib.read_stats(st, lib.TvStats).status == 7   # CBCT_ERR_TIMEOUT
+    assert 1.5 < waited < 60.0
+    rng = np.random.default_rng(23)
+    g = f32(0.02 * rng.random(og.vol_shape))
+    p = orc.TVParams(eps_tv=1e-3, max_inner=10)
+    ref = orc.rof_solve(og, g, 0.2, 0.5, p)
+    f = dev(g)
+    st2 = lib.stats_buffer(lib.TvStats)
+    tv = lib.TvParams(p.eps_tv, p.c, p.alpha, p.rel_tol, p.max_inner, p.max_backtracks, p.s0)
+    lib.cbct_tv_denoise(geom, dev(g), f, 0.2, 0.5, tv, ws, st2)
+    s = lib.read_stats(st2, lib.TvStats)
+    assert s.status == 0 and s.n_inner == ref.n_inner
+    assert rel_l2(host(f), ref.f) < TOL_CALL
