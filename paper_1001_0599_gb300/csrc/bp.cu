@@ -106,45 +106,31 @@ __device__ __forceinline__ void box_u_range(const DetGeom &d, float c, float s, 
 }
 
 // The z tent sum of one sample for one lane's voxel c: sum over the rows r
-// whose sample height is within one dz of z_c of (1 - sc |r - q|) * row value.
-template <int NR, bool PRESCALED>
-__device__ __forceinline__ float tent_rows(const DetGeom &d, const VolGeom &g, const float *pcol,
-                                           const void *gsino, size_t gbase, int st, const RayCol &rc,
-                                           bool staged, int s0, int s1, float q, float m, float sc)
+// whose sample height is within one dz of z_c of (1 - sc |r - q|) * row value,
+// rows inside the staged patch from shared memory and the others from the
+// sinogram in global memory (blocks whose patch did not fit, or rows beyond
+// it); the values are weighted by ds unless the sinogram is pre-weighted.
+template <bool PRESCALED>
+__device__ __forceinline__ float tent_rows_global(const DetGeom &d, const VolGeom &g, const float *pcol,
+                                                  const void *gsino, size_t gbase, int st, const RayCol &rc,
+                                                  bool staged, int s0, int s1, float q, float m, float sc)
 {
     float s = 0.f;
-    if (NR > 0 && staged) {
-        int r0 = (int)ceilf(q - m);
-        r0 = min(max(r0, s0), s1 - NR + 1);
-        const float dq = (float)r0 - q;
-        const float *p = pcol + r0;
-        float s2 = 0.f;
-#pragma unroll
-        for (int t = 0; t < (NR > 0 ? NR : 1); ++t) {
-            const float w = fmaxf(__fmaf_rn(-sc, fabsf(dq + (float)t), 1.f), 0.f);
-            if (t & 1)
-                s2 = __fmaf_rn(w, p[t], s2);
-            else
-                s = __fmaf_rn(w, p[t], s);
-        }
-        s += s2;
-    } else {
-        const int r_lo = max((int)ceilf(q - m), 0);
-        const int r_hi = min(min((int)floorf(q + m), d.nv - 1), r_lo + BP_MAX_ROWS);
-        for (int r = r_lo; r <= r_hi; ++r) {
-            const float w = fmaxf(__fmaf_rn(-sc, fabsf((float)r - q), 1.f), 0.f);
-            float val;
-            if (staged && r >= s0 && r <= s1) {
-                val = pcol[r];
-            } else {
-                val = ld_st(gsino, gbase + (size_t)r * d.nu, st);
-                if (!PRESCALED) {
-                    const float vl = (((float)r - d.cv) * d.dv) * rc.inv_lxy;
-                    val *= g.drho * sqrtf(1.f + vl * vl);
-                }
+    const int r_lo = max((int)ceilf(q - m), 0);
+    const int r_hi = min(min((int)floorf(q + m), d.nv - 1), r_lo + BP_MAX_ROWS);
+    for (int r = r_lo; r <= r_hi; ++r) {
+        const float w = fmaxf(__fmaf_rn(-sc, fabsf((float)r - q), 1.f), 0.f);
+        float val;
+        if (staged && r >= s0 && r <= s1) {
+            val = pcol[r];
+        } else {
+            val = ld_st(gsino, gbase + (size_t)r * d.nu, st);
+            if (!PRESCALED) {
+                const float vl = (((float)r - d.cv) * d.dv) * rc.inv_lxy;
+                val *= g.drho * sqrtf(1.f + vl * vl);
             }
-            s = __fmaf_rn(w, val, s);
         }
+        s = __fmaf_rn(w, val, s);
     }
     return s;
 }
@@ -261,10 +247,6 @@ __device__ __forceinline__ void interval_sums(const float *pcol, int s0, int s1,
     A = a + a2;
     B = b + b2;
 }
-
-#ifndef CBCT_BP_INTERVALS
-#define CBCT_BP_INTERVALS 1
-#endif
 
 // Add one sample's z sums to the group's columns its cell touches: a
 // warp-uniform switch over the 25 cells of the group and its one-voxel rim.
@@ -492,7 +474,7 @@ bp_kernel(VolGeom g, DetGeom d, const void *__restrict__ sino, int st, const flo
                         if (en.cell < 0) continue;  // uniform
                         const float *pcol = patch + en.col;
                         float sv[BP_ZC];
-                        if (CBCT_BP_INTERVALS && SPLIT > 1 && NR >= 16 && staged) {
+                        if (SPLIT > 1 && NR >= 16 && staged) {
                             // long tents (NR even, >= 16; measured: coarsest paper grid
                             // 1.28 -> 1.15 ms, while NR = 10 ran 2 % slower): interval
                             // sums, the interval below the warp's first voxel summed
@@ -543,8 +525,8 @@ bp_kernel(VolGeom g, DetGeom d, const void *__restrict__ sino, int st, const flo
                             for (int zc = 0; zc < BP_ZC; ++zc) {
                                 const int c = c_base + zc * 32 + lane;
                                 const float q = d.cv + ((float)c - g.cz) * en.m;
-                                sv[zc] = tent_rows<0, PRESCALED>(d, g, pcol, sino, gbase, st, rce, staged, s0,
-                                                                 s1, q, en.m, en.sc);
+                                sv[zc] = tent_rows_global<PRESCALED>(d, g, pcol, sino, gbase, st, rce, staged,
+                                                                     s0, s1, q, en.m, en.sc);
                             }
                         }
                         add_entry<ZC>(acc, en, sv);

@@ -150,3 +150,39 @@ def test_submit_validation(lib):
     with pytest.raises(lib.CbctError):
         srv.submit(g, rp, pinned_s, pinned_v)
     srv.close()
+
+
+def test_concurrent_submitters(lib):
+    # four host threads submit and wait at once; every scan still equals its
+    # direct reconstruction
+    import threading
+
+    import torch
+    scans = _scans(lib, ["small", "odd"], 4, seed=3)
+    ref = [_direct(lib, g, p, s) for _, g, p, s in scans]
+    srv = lib.Server(use_graphs=True)
+    outs = [None] * len(scans)
+    errors = []
+
+    def worker(k):
+        try:
+            for i in range(k, len(scans), 4):
+                _, g, p, s = scans[i]
+                h_vol = torch.empty(g.vol_shape).pin_memory()
+                t = srv.submit(g, p, s, h_vol)
+                r = srv.wait(t)
+                outs[i] = (h_vol.numpy().copy(), r.status)
+        except Exception as e:   # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    info = srv.query()
+    srv.close()
+    assert not errors
+    assert info.completed == len(scans)
+    for (v, status), (rv, _) in zip(outs, ref):
+        assert status == 0 and np.array_equal(v, rv)
