@@ -216,3 +216,27 @@ def test_back_projection_continuum_limit_is_eq6(orc):
     rel = np.abs(bp[inner] - scale * e6[inner]) / np.abs(scale * e6[inner])
     assert rel.max() < 0.02
     assert np.median(rel) < 0.005
+
+
+def test_count_terms_single_voxel_closed_forms(orc):
+    # one 2 mm voxel at the isocentre, one pixel at the detector centre, in-plane
+    # sample spacing 1 mm on a lattice that hits the isocentre (SAD = 100 mm):
+    # along x (0 degrees) the samples at -1, 0, +1 mm lie inside the voxel's
+    # open trilinear support (|x| < 2 mm), each with one non-zero corner (the
+    # other corners are outside the one-voxel grid or carry weight 0): 3 terms.
+    # Along the diagonal (45 degrees) the samples at in-plane offsets -2..+2 mm
+    # reach |x|, |y| = 1.41 mm < 2 mm: 5 terms.
+    for theta, expect in ((0.0, 3), (np.pi / 4, 5)):
+        g = orc.Geometry(1, 1, 1, 2.0, 2.0, 2.0, 1, 1, 1.0, 1.0, 100.0, 150.0, np.array([theta]), 0.5)
+        assert orc.count_terms(g) == expect
+
+
+def test_forward_rays_equal_full_projection(orc):
+    g = orc.Geometry(7, 6, 5, 2.0, 2.0, 2.0, 11, 9, 1.7, 1.9, 200.0, 320.0,
+                     np.linspace(0, 2 * np.pi, 4, endpoint=False), 0.5)
+    rng = np.random.default_rng(31)
+    f = rng.random(g.vol_shape)
+    full = orc.forward_project(g, f)
+    view, iv, iu = np.meshgrid(np.arange(g.n_views), np.arange(g.nv), np.arange(g.nu), indexing="ij")
+    rays = orc.forward_rays(g, f, view.ravel(), iv.ravel(), iu.ravel())
+    np.testing.assert_array_equal(rays, full.ravel())
