@@ -687,10 +687,11 @@ def roofline(prof, prof_levels, wl):
     name, (n, ms) = max(prof.items(), key=lambda kv: kv[1][1])
     if n == 0 or ms <= 0:
         return None
-    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count \
+        if torch.cuda.is_available() else 152
     peaks = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     try:
         with open(os.path.join(ROOT, "tests", "golden", "nnz.json")) as fh:
             nnz = json.load(fh)[wl.name]

@@ -1,0 +1,75 @@
+"""Host logic of the benchmark (no GPU): workload descriptions of both arms,
+the roofline and bandwidth arithmetic on given timings, the source-matched
+traffic lookup, the serving stream and the FIFO latency model."""
+import argparse
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _args(**kw):
+    d = dict(power_fine=4, gradient="matched", workload="paper", storage="f32")
+    d.update(kw)
+    return argparse.Namespace(**d)
+
+
+def test_workload_descriptions(bench):
+    w, m = bench.workload_description(_args())
+    assert "256x256x128" in w and "4 per finer level" in w and m == bench.METRIC
+    w, m = bench.workload_description(_args(workload="lowdose", storage="bf16", gradient="eq6"))
+    assert "256x256x256" in w and "360 views" in w and "bf16" in w and "Eq. 6" in w and "low-dose" in m
+    w, _ = bench.workload_description(_args(power_fine=0))
+    assert "20 power iterations per level" in w
+
+
+def test_roofline_and_bandwidth_arithmetic(bench):
+    from paper_1001_0599_gb300 import synthetic
+    wl = synthetic.workload("paper")
+    nnz0 = 19262253600
+    # 30 finest-level transpose steps of 5 ms, fewer elsewhere
+    prof = {"back_project_step": (100, 400.0), "forward_residual": (100, 200.0), "rof_persistent": (100, 20.0)}
+    levels = {0: {"back_project_step": (30, 150.0), "forward_residual": (30, 80.0)},
+              1: {"back_project_step": (30, 70.0)}, 2: {"back_project_step": (40, 50.0)}}
+    r = bench.roofline(prof, levels, wl)
+    assert r["kernel"] == "back_project_step" and r["level"] == 0 and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(2 * nnz0 / 5e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert set(r["levels"]) == {0, 1, 2}
+    b = bench.projector_bandwidth(levels, wl)
+    nvox, nray = 256 * 256 * 128, 40 * 384 * 512
+    assert b["back_project_step"]["algorithmic_bytes"] == 4 * (nray + 2 * nvox)
+    assert b["forward_residual"]["algorithmic_gbs"] == pytest.approx(4 * (nvox + 2 * nray) / (80.0 / 30 / 1e3) / 1e9)
+    assert b["forward_residual"]["samples_per_s"] == pytest.approx(nnz0 / 8 / (80.0 / 30 / 1e3))
+
+
+def test_traffic_follows_the_sources(bench, tmp_path, monkeypatch):
+    # a capture counts only while the kernel's sources hash as they did
+    import json
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
+        {"back_project_step/paper/L0": {"dram_bytes_per_launch": 123, "sources_sha1": "abc"}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "sources_sha1", lambda names: "abc")
+    assert bench.measured_traffic("back_project_step", "paper", 0) == 123
+    assert bench.measured_traffic("back_project_step", "lowdose", 0) is None
+    monkeypatch.setattr(bench, "sources_sha1", lambda names: "def")
+    assert bench.measured_traffic("back_project_step", "paper", 0) is None
+
+
+def test_serve_stream_and_fifo_model(bench):
+    a, b = bench.serve_stream(64), bench.serve_stream(64)
+    assert a == b and len(a) == 64
+    assert {x[0] for x in a} <= set(range(len(bench.SERVE_GRIDS)))
+    # one-at-a-time queue: the second job waits for the first
+    assert bench.fifo_latencies([0.0, 0.5, 5.0], [1.0, 1.0, 1.0]) == [1.0, 1.5, 1.0]
