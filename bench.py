@@ -489,6 +489,10 @@ def serve_bench(args, rank, world, local):
     stream = serve_stream(args.serve_scans)
     tv = cbct.TvParams.paper(eps_tv=1e-5)
     params = cbct.make_recon_params(0.05, SERVE_ITERS, tv, power_iters=20, clamp=True, power_iters_fine=4)
+    # the service may store sinograms and the projector's volume copy at reduced
+    # precision; the sequential baseline is plain FP32 storage
+    sparams = cbct.make_recon_params(0.05, SERVE_ITERS, tv, power_iters=20, clamp=True, power_iters_fine=4,
+                                     storage=args.storage)
     geoms, truths, scans = {}, {}, []
     for i, (gi, di, vi) in enumerate(stream):
         nx, ny, nz, dx, dy, dz = SERVE_GRIDS[gi]
@@ -543,7 +547,8 @@ def serve_bench(args, rank, world, local):
     srv = cbct.Server(use_graphs=True)
     outs = [torch.empty(g.vol_shape, dtype=torch.float32).pin_memory() for _, g, _, _ in scans]
     # warm-up: one scan per shape captures its slot's graph
-    warm = [srv.submit(g, params, scans[[s[0] for s in scans].index(key)][2], outs[0].new_empty(g.vol_shape).pin_memory())
+    warm = [srv.submit(g, sparams, scans[[s[0] for s in scans].index(key)][2],
+                       outs[0].new_empty(g.vol_shape).pin_memory())
             for key, (wl, g) in geoms.items()]
     for t in warm:
         srv.wait(t)
@@ -559,7 +564,7 @@ def serve_bench(args, rank, world, local):
             delay = t0 + a - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            tickets.append(srv.submit(g, params, y, o))
+            tickets.append(srv.submit(g, sparams, y, o))
         res = [srv.wait(t) for t in tickets]
         lat = [r.t_done - r.t_submit for r in res]
         span = max(r.t_done for r in res) - min(r.t_submit for r in res)
@@ -578,17 +583,20 @@ def serve_bench(args, rank, world, local):
     srv.close()
     # back-to-back stream (all scans submitted at once): the throughput ceiling
     srv = cbct.Server(use_graphs=True)
-    for t in [srv.submit(g, params, scans[[s[0] for s in scans].index(key)][2],
+    for t in [srv.submit(g, sparams, scans[[s[0] for s in scans].index(key)][2],
                          outs[0].new_empty(g.vol_shape).pin_memory()) for key, (wl, g) in geoms.items()]:
         srv.wait(t)
     t0 = time.perf_counter()
-    tickets = [srv.submit(g, params, y, o) for (key, g, y, gi), o in zip(scans, outs)]
+    tickets = [srv.submit(g, sparams, y, o) for (key, g, y, gi), o in zip(scans, outs)]
     res = [srv.wait(t) for t in tickets]
     burst = time.perf_counter() - t0
     srv.close()
+    rms_srv = [float(np.sqrt(np.mean((o.numpy().reshape(g.vol_shape) - truths[gi]) ** 2)))
+               for (key, g, y, gi), o in zip(scans, outs)]
     line = {"metric": "serving: scan latency p50/p99 (s) and scans/min, mixed 64-scan stream",
             "mode": "serve", "value": results[-1]["p99_s"] if results else None, "unit": "s (p99 at the highest load)",
-            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32" if args.storage == "f32" else f"f32 ({args.storage} storage)", "data": "synthetic",
             "config": {"workload": f"{len(scans)} scans; grids {SERVE_GRIDS}; detectors {SERVE_DETECTORS}; "
                                    f"views {SERVE_VIEWS}; 50 FBS-TV iterations (multigrid 20/15/15), "
                                    "lambda 0.05, Poisson 5e4 photons; stream seed 10",
@@ -596,8 +604,11 @@ def serve_bench(args, rank, world, local):
             "sequential": {"scans_per_min": 60.0 * capacity, "total_s": seq_total,
                            "mean_service_s": float(np.mean(service))},
             "server_burst": {"scans_per_min": 60.0 * len(scans) / burst, "total_s": burst},
-            "loads": results, "bit_identical_to_sequential": bool(identical),
-            "rms_error_vs_phantom": float(np.mean(rms)),
+            "loads": results, "storage": args.storage,
+            "bit_identical_to_sequential": bool(identical) if args.storage == "f32" else None,
+            "rms_error_vs_phantom": {"sequential_f32": float(np.mean(rms)), "server": float(np.mean(rms_srv)),
+                                     "max_rel_diff_per_scan": float(max(abs(a - b) / b for a, b in
+                                                                        zip(rms_srv, rms)))},
             "server": {"slots": int(info.slots), "graphs_captured": int(info.graphs_captured),
                        "graph_failures": int(info.graph_failures), "evictions": int(info.evictions),
                        "peak_arena_gb": info.peak_bytes_in_use / 1e9, "arena_gb": info.arena_bytes / 1e9},
