@@ -155,3 +155,29 @@ def test_warm_started_power_iteration_converges_to_eigvalsh(orc):
     L_cold, _ = orc.power_lipschitz_from(g, np.ones(g.vol_shape), 25)
     assert L_cold == pytest.approx(orc.power_lipschitz(g, 25), rel=1e-14)
     assert L_cold <= lam_max * (1 + 1e-12)
+
+
+def test_eq6_step_tends_to_matched_step(orc):
+    # Step 1 through Eq. 6 (with the voxel volume / (2 du dv) factor) approaches
+    # the matched gradient step on a smooth residual: with lambda = 0 and no
+    # clamp, one iteration of each moves f by nearly the same amount inside the
+    # volume (pins the scale factor and its sign)
+    n = 24
+    g = orc.Geometry(n, n, 16, 1.0, 1.0, 1.0, 120, 90, 0.5, 0.5, 600.0, 900.0,
+                     np.array([0.0, 1.1, 3.7]), 0.5)
+    rng = np.random.default_rng(41)
+    f0 = 0.02 * rng.random(g.vol_shape)
+    uu = (np.arange(g.nu) - 0.5 * (g.nu - 1)) * g.du
+    vv = (np.arange(g.nv) - 0.5 * (g.nv - 1)) * g.dv
+    T = np.broadcast_to(1.0 + 0.3 * np.cos(uu[None, None, :] / 9.0) * np.exp(-(vv[None, :, None] / 30.0) ** 2),
+                        g.sino_shape).copy()
+    y = orc.forward_project(g, f0) - T      # residual P f0 - y = T, smooth
+    tau = 1.0 / orc.power_lipschitz(g, 20)
+    p = orc.TVParams()
+    fm, f6 = f0.copy(), f0.copy()
+    orc.fbs_iteration(g, y, fm, 0.0, tau, p, clamp=False)
+    orc.fbs_iteration_eq6(g, y, f6, 0.0, tau, p, clamp=False)
+    inner = (slice(4, n - 4), slice(4, n - 4), slice(3, 13))
+    dm, d6 = (fm - f0)[inner], (f6 - f0)[inner]
+    assert np.all(dm < 0) and np.all(d6 < 0)       # both descend along -P^T T
+    assert np.max(np.abs(d6 - dm) / np.abs(dm)) < 0.03
