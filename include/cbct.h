@@ -148,8 +148,9 @@ typedef struct {
 /* ---- geometry ---------------------------------------------------------- */
 
 /* Validate desc and build the handle (Eq. 1's geometry, Fig. 1). Allocates
- * the device ray tables on the current device (the only device allocation
- * of the library). Returns INVALID_ARG for a bad description, OUT_OF_MEMORY
+ * the device ray tables on the current device (with the serving arena of
+ * cbct_server_create, the library's only device allocations). Returns
+ * INVALID_ARG for a bad description, OUT_OF_MEMORY
  * or CUDA for allocation/copy failures; *out is NULL on failure. */
 cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct_geometry **out);
 void cbct_geometry_destroy(cbct_geometry *geom);
@@ -212,12 +213,14 @@ cbct_status cbct_gradient_step(const cbct_geometry *geom, const float *d_r, cons
 /* ---- reduced-precision storage ----------------------------------------- */
 
 /* P (Eq. 1) of a volume stored as `storage` into a sinogram stored the same
- * way (FP32 arithmetic in between). Reduced storage needs the shared-memory
- * sheet projector (nv <= 1024 and nz <= 760); otherwise CBCT_ERR_UNSUPPORTED. */
+ * way (FP32 arithmetic in between; each stored value rounded to nearest).
+ * Both arrays 16-byte aligned, in the layouts above. Reduced storage needs
+ * the shared-memory sheet projector (nv <= 1024 and nz <= 760); otherwise
+ * CBCT_ERR_UNSUPPORTED. An unknown storage value is CBCT_ERR_INVALID_ARG. */
 cbct_status cbct_forward_project_ex(const cbct_geometry *geom, const void *d_vol, void *d_sino, int storage,
                                     void *stream);
 /* The matched transpose of a sinogram stored as `storage`, into an FP32
- * volume (overwritten). */
+ * volume (overwritten); the same argument rules as cbct_forward_project_ex. */
 cbct_status cbct_back_project_ex(const cbct_geometry *geom, const void *d_sino, int storage, float *d_vol,
                                  void *stream);
 /* n elements from src_storage to dst_storage (round to nearest). */
