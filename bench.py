@@ -296,7 +296,8 @@ def main():
     tv = cbct.TvParams.paper(eps_tv=1e-5)
     if args.mode == "one-iteration":
         iters = (1,) + (0,) * args.level   # coarsest level listed first
-        params = cbct.make_recon_params(wl.lam, iters, tv, taus=[1.28e-5] * (args.level + 1), clamp=True)
+        params = cbct.make_recon_params(wl.lam, iters, tv, taus=[1.28e-5] * (args.level + 1), clamp=True,
+                                        gradient=args.gradient, storage=args.storage)
     else:
         params = cbct.make_recon_params(wl.lam, wl.iters, tv, power_iters=20, clamp=True,
                                         power_iters_fine=args.power_fine, gradient=args.gradient,
