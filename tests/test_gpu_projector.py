@@ -136,20 +136,24 @@ def _columns_of_p(orc, og, j, views):
                 vv.append(k)
                 ii.append(iv)
                 uu.append(iu)
+    vv, ii, uu = (np.array(x, dtype=np.int64) for x in (vv, ii, uu))
+    if vv.size == 0:   # the voxel projects outside the detector in every view
+        return vv, ii, uu, np.zeros(0)
     e = np.zeros(og.vol_shape)
     e[a, b, c] = 1.0
     w = orc.forward_rays(og, e, vv, ii, uu)
-    return np.array(vv), np.array(ii), np.array(uu), w
+    return vv, ii, uu, w
 
 
 @pytest.mark.slow
-def test_paper_scale_sampled_parity(lib, orc):
-    """Full-size workload (256x256x128, 40 views, 512x384) in the launch
-    configuration of the benchmark: P on 400 sampled rays, P^T on sampled
-    voxels through their oracle columns."""
+@pytest.mark.parametrize("name", ["paper", "lowdose"])
+def test_paper_scale_sampled_parity(lib, orc, name):
+    """Full-size workloads (256x256x128, 40 views, 512x384; 256^3, 360 views)
+    in the launch configuration of the benchmark: P on 400 sampled rays, P^T on
+    sampled voxels through their oracle columns."""
     import torch
     from paper_1001_0599_gb300 import synthetic
-    wl = synthetic.workload("paper")
+    wl = synthetic.workload(name)
     g = lib.geometry_from_workload(wl)
     og = orc.Geometry.from_workload(wl)
     truth = f32(synthetic.voxelise(synthetic.make_phantom(wl), wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz))
