@@ -43,12 +43,14 @@ eq6_kernel(VolGeom g, DetGeom d, const float *__restrict__ T, const float *__res
             const float xr = x * cs.x + y * cs.y;       // depth along the central ray
             const float yr = -x * cs.y + y * cs.x;
             const float depth = xr + d.sad;             // x' - x_s
-            const float inv_depth = 1.f / depth;
+            const float inv_depth = __frcp_rn(depth);     // correctly rounded, as 1 / depth
             const float us = -yr * L0 * inv_depth;      // Eq. A6
             const float vs = z * L0 * inv_depth;
             const float l2 = depth * depth + yr * yr + z * z;
             const float Lsq = L0 * L0 + us * us + vs * vs;
-            const float w = 2.f * Lsq * sqrtf(Lsq) / (L0 * l2);   // 2 L^3 / (L0 l^2)
+            // 2 L^3 / (L0 l^2): L = Lsq rsqrt(Lsq) and one reciprocal (a few ulp of
+            // FP32, far inside the detector-coordinate rounding of the sample)
+            const float w = 2.f * Lsq * (Lsq * rsqrtf(Lsq)) * __frcp_rn(L0 * l2);
             // bilinear detector interpolation, zero outside
             const float fu = __fmaf_rn(us, d.inv_du, d.cu), fv = __fmaf_rn(vs, d.inv_dv, d.cv);
             const float u0f = floorf(fu), v0f = floorf(fv);
