@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp16"],
                     help="storage type of the sinograms and of the projector's volume copy "
                          "(FP32 arithmetic throughout)")
-    ap.add_argument("--workload", default="paper", choices=["paper", "lowdose"],
-                    help="paper: 256x256x128, 40 views; lowdose: 256^3, 360 views, 1e4 photons")
+    ap.add_argument("--workload", default="paper", choices=["paper", "lowdose", "cube40"],
+                    help="paper: 256x256x128, 40 views; lowdose: 256^3, 360 views, 1e4 photons; "
+                         "cube40: 256^3, 40 views")
     ap.add_argument("--level", type=int, default=0,
                     help="one-iteration mode: multigrid level (0 = finest)")
     ap.add_argument("--mode", default="recon", choices=["recon", "one-iteration", "serve"],
@@ -205,6 +206,9 @@ def workload_description(args):
         workload = workload.replace("paper-scale: 256x256x128 voxels", "low-dose: 256x256x256 voxels").replace(
             "40 views/360 deg", "360 views/360 deg").replace("Poisson 5e4", "Poisson 1e4")
         metric = "recon sec at 256^3 x 360 views (low-dose workload)"
+    if args.workload == "cube40":
+        workload = workload.replace("paper-scale: 256x256x128 voxels", "cubic: 256x256x256 voxels")
+        metric = "recon sec at 256^3 x 40 views"
     if args.storage != "f32":
         workload += (f"; measured sinogram, residual and the projector's volume copy stored as {args.storage} "
                      "(FP32 arithmetic, FP64 sums)")

@@ -78,6 +78,8 @@ def workload(name: str) -> Workload:
                   head-and-neck-like phantom, 5e4 photons, 3-level multigrid
                   (64 -> 128 -> 256 in-plane), 100 FBS iterations (40/30/30).
     lowdose    -- 256^3 at 1 mm, 512x384 detector, 360 views, 1e4 photons.
+    cube40     -- 256^3 at 1 mm, 512x384 detector, 40 views, 5e4 photons, 3-level
+                  multigrid (40/30/30): the paper-scale schedule on a cubic volume.
     autograd   -- 128^3 at 2 mm, 256x192 detector at 1.56 mm, 60 views.
     """
     if name == "small":
@@ -91,6 +93,10 @@ def workload(name: str) -> Workload:
     if name == "lowdose":
         return Workload("lowdose", 256, 256, 256, 1.0, 1.0, 1.0, 512, 384, 0.78, 0.78, 360,
                         photons=1e4, phantom="head_neck", phantom_seed=5, noise_seed=6,
+                        lam=0.05, iters=(40, 30, 30))
+    if name == "cube40":
+        return Workload("cube40", 256, 256, 256, 1.0, 1.0, 1.0, 512, 384, 0.78, 0.78, 40,
+                        photons=5e4, phantom="head_neck", phantom_seed=5, noise_seed=6,
                         lam=0.05, iters=(40, 30, 30))
     if name == "autograd":
         return Workload("autograd", 128, 128, 128, 2.0, 2.0, 2.0, 256, 192, 1.56, 1.56, 60,

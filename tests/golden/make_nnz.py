@@ -15,7 +15,7 @@ from paper_1001_0599_gb300 import synthetic  # noqa: E402
 
 def main():
     out = {"_doc": "non-zero weights of P per workload and multigrid level (0 = finest), from orc_count_terms"}
-    for name, levels in (("small", 1), ("paper", 3), ("lowdose", 3)):
+    for name, levels in (("small", 1), ("paper", 3), ("lowdose", 3), ("cube40", 3)):
         wl = synthetic.workload(name)
         g = orc.Geometry.from_workload(wl)
         out[name] = {str(l): orc.count_terms(g.coarse(2 ** l) if l else g) for l in range(levels)}
