@@ -302,7 +302,9 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
         v.drho = (float)drho;
         v.cols = L.d_cols;
         v.bp_cap = 0;
+        v.bs_cap = 0;
         v.bp_cap = bp_patch_floats(v, det, d.angles);
+        v.bs_cap = bs_patch_floats(v, det, d.angles);
         L.drho = drho;
         L.dx = dx;
         L.dy = dy;

@@ -21,7 +21,7 @@
 // z tent weight max(0, 1 - sc |r - q|) zeroes the rows outside the tent, and
 // NR (>= the largest number of rows a voxel's tent can span on this grid) is
 // a template parameter, so the row loop is fully unrolled.
-#include "cbct_internal.cuh"
+#include "bp_common.cuh"
 
 #ifndef BP_MODE_UNIT
 #define BP_MODE_UNIT 0
@@ -36,15 +36,10 @@
 
 namespace cbct {
 
-constexpr int BP_G = 4;               // a warp owns a BP_G x BP_G group of voxel columns
 constexpr int BP_GX = 2, BP_GY = 2;   // groups per block along x, y
 constexpr int BP_TX = BP_G * BP_GX, BP_TY = BP_G * BP_GY;   // voxel columns per block
 constexpr int BP_WARPS = BP_GX * BP_GY;
 constexpr int BP_MAX_ROWS = 64;       // runtime row-loop bound (generic variant)
-
-struct Box {
-    float xlo, xhi, ylo, yhi;
-};
 
 // One sample of a warp's footprint list: xy cell relative to the group in the
 // low 8 bits and the detector column above them (-1: outside the group),
@@ -55,6 +50,12 @@ struct __align__(16) SampleEntry {
     float w00, w01, w10, w11, sc, m;
 };
 constexpr int BP_ENTRIES = 96;    // entries per warp and batch
+
+template <int ZC>
+__device__ __forceinline__ void add_entry(float (&acc)[BP_G][BP_G][ZC], const SampleEntry &en, const float (&sv)[ZC])
+{
+    add_entry_cell<ZC>(acc, en.cell & 255, en.w00, en.w01, en.w10, en.w11, sv);
+}
 
 // Warps per column group for a row count NR: voxels whose z tent spans many
 // detector rows come with tall staged patches and so with few blocks per SM;
@@ -78,32 +79,6 @@ struct BpLaunch {
 
 template <int MODE, bool P>
 cudaError_t bp_dispatch(int zc, int nr, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const BpLaunch &L);
-
-__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.f, x); }
-
-// detector columns [iu0, iu1] that can see the xy box in view (c, s), and the
-// box's depth range along the central ray
-__device__ __forceinline__ void box_u_range(const DetGeom &d, float c, float s, const Box &bx,
-                                            int &iu0, int &iu1, float &xr_lo, float &xr_hi)
-{
-    float umin = 3.0e38f, umax = -3.0e38f;
-    xr_lo = 3.0e38f;
-    xr_hi = -3.0e38f;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const float x = (k & 1) ? bx.xhi : bx.xlo;
-        const float y = (k & 2) ? bx.yhi : bx.ylo;
-        const float xr = x * c + y * s;
-        const float yr = -x * s + y * c;
-        const float u = -yr * d.sdd * fast_rcp(xr + d.sad);
-        umin = fminf(umin, u);
-        umax = fmaxf(umax, u);
-        xr_lo = fminf(xr_lo, xr);
-        xr_hi = fmaxf(xr_hi, xr);
-    }
-    iu0 = max((int)floorf(umin * d.inv_du + d.cu) - 1, 0);
-    iu1 = min((int)ceilf(umax * d.inv_du + d.cu) + 1, d.nu - 1);
-}
 
 // The z tent sum of one sample for one lane's voxel c: sum over the rows r
 // whose sample height is within one dz of z_c of (1 - sc |r - q|) * row value,
@@ -135,32 +110,6 @@ __device__ __forceinline__ float tent_rows_global(const DetGeom &d, const VolGeo
     return s;
 }
 
-// Stage rows [s0, s0 + h) x columns [iu0, iu0 + w) of one view's sinogram
-// into the column-major patch (pitch hp), zero outside the detector, weighted
-// by ds unless the sinogram is pre-weighted.
-template <bool PRESCALED, int NWARPS, typename T>
-__device__ __forceinline__ void stage_patch(float *patch, const T *__restrict__ src, const VolGeom &g, const DetGeom &d,
-                                            int view, int iu0, int s0, int w, int h, int hp, int wid, int lane)
-{
-    const int nu = d.nu, nv = d.nv;
-    for (int r = wid; r < h; r += NWARPS) {
-        const int iv = s0 + r;
-        const bool in = iv >= 0 && iv < nv;
-        for (int cc = lane; cc < w; cc += 32) {
-            const int iu = iu0 + cc;
-            float val = 0.f;
-            if (in) {
-                val = ldt(src + (size_t)iv * nu + iu);
-                if (!PRESCALED) {
-                    const float vl = (((float)iv - d.cv) * d.dv) * g.cols[(size_t)view * nu + iu].inv_lxy;
-                    val *= g.drho * sqrtf(1.f + vl * vl);
-                }
-            }
-            patch[cc * hp + r] = val;
-        }
-    }
-}
-
 // Staged variant only (no global fallback): NR rows from the padded patch.
 template <int NR>
 __device__ __forceinline__ float tent_rows_staged(const float *pcol, bool staged, int s0, int s1, float q, float m,
@@ -182,28 +131,6 @@ __device__ __forceinline__ float tent_rows_staged(const float *pcol, bool staged
         }
     }
     return s + s2;
-}
-
-// Add a sample's z sums into the (up to four) columns of the warp's G x G
-// group that its xy cell (RA, RB) (relative to the group) touches; corners
-// outside the group belong to a neighbouring group's warp.
-template <int IA, int IB, int ZC>
-__device__ __forceinline__ void add_one(float (&acc)[BP_G][BP_G][ZC], float w, const float (&s)[ZC])
-{
-    if constexpr (IA >= 0 && IA < BP_G && IB >= 0 && IB < BP_G) {
-#pragma unroll
-        for (int zc = 0; zc < ZC; ++zc) acc[IA][IB][zc] = __fmaf_rn(w, s[zc], acc[IA][IB][zc]);
-    }
-}
-
-template <int RA, int RB, int ZC>
-__device__ __forceinline__ void add_corners(float (&acc)[BP_G][BP_G][ZC], float w00, float w01, float w10,
-                                            float w11, const float (&s)[ZC])
-{
-    add_one<RA, RB, ZC>(acc, w00, s);
-    add_one<RA, RB + 1, ZC>(acc, w01, s);
-    add_one<RA + 1, RB, ZC>(acc, w10, s);
-    add_one<RA + 1, RB + 1, ZC>(acc, w11, s);
 }
 
 // NR > 0: rows per (lane, sample) fully unrolled; NR == 0: runtime loop.
@@ -246,30 +173,6 @@ __device__ __forceinline__ void interval_sums(const float *pcol, int s0, int s1,
     }
     A = a + a2;
     B = b + b2;
-}
-
-// Add one sample's z sums to the group's columns its cell touches: a
-// warp-uniform switch over the 25 cells of the group and its one-voxel rim.
-template <int ZC>
-__device__ __forceinline__ void add_entry(float (&acc)[BP_G][BP_G][ZC], const SampleEntry &en, const float (&sv)[ZC])
-{
-    switch (en.cell & 255) {
-#define CBCT_CORNER(RA, RB)                                                                         \
-    case ((RA) + 1) * (BP_G + 1) + ((RB) + 1):                                                      \
-        add_corners<RA, RB, ZC>(acc, en.w00, en.w01, en.w10, en.w11, sv);                           \
-        break;
-#define CBCT_CORNER_ROW(RA)                                                                         \
-    CBCT_CORNER(RA, -1) CBCT_CORNER(RA, 0) CBCT_CORNER(RA, 1) CBCT_CORNER(RA, 2) CBCT_CORNER(RA, 3)
-        CBCT_CORNER_ROW(-1)
-        CBCT_CORNER_ROW(0)
-        CBCT_CORNER_ROW(1)
-        CBCT_CORNER_ROW(2)
-        CBCT_CORNER_ROW(3)
-#undef CBCT_CORNER_ROW
-#undef CBCT_CORNER
-    default:
-        break;
-    }
 }
 
 // samples taken together in the transpose's main loop (short tents)
@@ -621,6 +524,8 @@ static int sm_count()
 
 size_t bp_split_floats(const VolGeom &v, const DetGeom &d)
 {
+    // the stream-K transpose keeps its tile partials and arrival counters here
+    if (bs_usable(v, d)) return bs_scratch_floats(v, d) + bs_counter_count(v, d);
     const int gcount = bp_view_groups(v, d);
     return gcount > 1 ? (size_t)gcount * v.nx * v.ny * v.nz : 0;
 }
@@ -641,7 +546,7 @@ static double support_r(const VolGeom &v)
 
 // Largest number of detector rows one voxel's z tent can cover on this grid:
 // floor(2 m) + 1 with m = 1/sc at the smallest sc = rho dv / (L_xy dz).
-static int bp_rows_needed(const VolGeom &v, const DetGeom &d)
+int bp_rows_needed(const VolGeom &v, const DetGeom &d)
 {
     const double R = support_r(v);
     const double umax = 0.5 * (d.nu - 1) * d.du;
@@ -666,8 +571,15 @@ static int bp_nr_variant(const VolGeom &v, const DetGeom &d)
 // global memory instead.
 int bp_patch_floats(const VolGeom &v, const DetGeom &d, const double *angles)
 {
-    const int zc = bp_zc(v), tz = 32 * zc, nr = bp_nr_variant(v, d);
-    const int nbx = (v.nx + BP_TX - 1) / BP_TX, nby = (v.ny + BP_TY - 1) / BP_TY, nbz = bp_zblocks(v);
+    const long cap_max = 48L * 1024L;   // floats: 192 KB
+    return (int)std::min<long>(bp_patch_floats_tile(v, d, angles, 32 * bp_zc(v), bp_nr_variant(v, d)), cap_max);
+}
+
+// The same for tiles of BP_TX x BP_TY columns and tz z values with nr zero
+// rows of padding on each side.
+int bp_patch_floats_tile(const VolGeom &v, const DetGeom &d, const double *angles, int tz, int nr)
+{
+    const int nbx = (v.nx + BP_TX - 1) / BP_TX, nby = (v.ny + BP_TY - 1) / BP_TY, nbz = (v.nz + tz - 1) / tz;
     const double cx = 0.5 * (v.nx - 1), cy = 0.5 * (v.ny - 1), cz = 0.5 * (v.nz - 1);
     const double cu = 0.5 * (d.nu - 1), cv = 0.5 * (d.nv - 1);
     long best = 0;
@@ -702,8 +614,7 @@ int bp_patch_floats(const VolGeom &v, const DetGeom &d, const double *angles)
                 }
             }
     }
-    const long cap_max = 48L * 1024L;   // floats: 192 KB
-    return (int)std::min(best, cap_max);
+    return (int)std::min<long>(best, (long)INT32_MAX);
 }
 
 // Dynamic shared memory of a transpose launch on this grid.
@@ -819,6 +730,7 @@ int bp_view_groups(const VolGeom &v, const DetGeom &d)
 
 int bp_partials_count(const VolGeom &v, const DetGeom &d, bool split)
 {
+    if (bs_usable(v, d)) return bs_partials_count(v);
     if (split && bp_view_groups(v, d) > 1) return BPC_BLOCKS;
     return ((v.nx + BP_TX - 1) / BP_TX) * ((v.ny + BP_TY - 1) / BP_TY) * bp_zblocks(v);
 }
@@ -907,6 +819,16 @@ cudaError_t launch_back_st(const VolGeom &v, const DetGeom &d, const void *sino,
                            float *out, const double *d_scale, double scale_val, double kappa,
                            double *partials, int mode, int prescaled, float *split_ws, cudaStream_t s)
 {
+    if (bs_usable(v, d) && (mode != 2 || prescaled)) {
+        const int kid = mode == 1 ? K_BP_STEP : K_BP;
+        unsigned int *counters =
+            split_ws ? reinterpret_cast<unsigned int *>(split_ws + bs_scratch_floats(v, d)) : nullptr;
+        launch_begin(kid, s);
+        const cudaError_t e = launch_bs(v, d, sino, st, f, out, d_scale, scale_val, kappa, partials, mode, prescaled,
+                                        split_ws, counters, s);
+        launch_end(kid, s);
+        return e;
+    }
     const int zc = bp_zc(v), zblocks = bp_zblocks(v);
     const int groups = split_ws ? bp_view_groups(v, d) : 1;
     const int vpg = (d.n_views + groups - 1) / groups;

@@ -39,6 +39,7 @@ struct VolGeom {
     float drho;                // in-plane sample spacing
     const RayCol *cols;        // [n_views][nu]
     int bp_cap;                // largest staged detector patch of the transpose, floats (0: bound)
+    int bs_cap;                // staged patch of the stream-K transpose (bps.cu), floats (0: not used)
 };
 
 struct DetGeom {
@@ -245,6 +246,8 @@ int bp_view_groups(const VolGeom &v, const DetGeom &d);
 size_t bp_split_floats(const VolGeom &v, const DetGeom &d);
 size_t bp_smem_bytes(const VolGeom &v, const DetGeom &d);
 int bp_patch_floats(const VolGeom &v, const DetGeom &d, const double *angles);
+int bp_patch_floats_tile(const VolGeom &v, const DetGeom &d, const double *angles, int tz, int nr);
+int bp_rows_needed(const VolGeom &v, const DetGeom &d);   // most detector rows one voxel's z tent spans
 size_t bp_smem_bound(const VolGeom &v, const DetGeom &d);
 cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, const float *f,
                         float *out, const double *d_scale, double scale_val, double kappa,
@@ -253,6 +256,19 @@ cudaError_t launch_back(const VolGeom &v, const DetGeom &d, const float *sino, c
 cudaError_t launch_back_st(const VolGeom &v, const DetGeom &d, const void *sino, int st, const float *f,
                            float *out, const double *d_scale, double scale_val, double kappa,
                            double *partials, int mode, int prescaled, float *split_ws, cudaStream_t s);
+
+// Stream-K transpose for short z tents (bps.cu): the same modes 0-2 as
+// launch_back. Grids it serves (bs_usable) give one mode-2 partial per column
+// tile (bs_partials_count). scratch (bs_scratch_floats floats) and counters
+// (bs_counter_count) may be null: every block then takes whole tiles.
+int bs_patch_floats(const VolGeom &v, const DetGeom &d, const double *angles);
+bool bs_usable(const VolGeom &v, const DetGeom &d);
+int bs_partials_count(const VolGeom &v);
+size_t bs_scratch_floats(const VolGeom &v, const DetGeom &d);
+size_t bs_counter_count(const VolGeom &v, const DetGeom &d);
+cudaError_t launch_bs(const VolGeom &v, const DetGeom &d, const void *sino, int st, const float *f, float *out,
+                      const double *d_scale, double scale_val, double kappa, double *partials, int mode,
+                      int prescaled, float *scratch, unsigned int *counters, cudaStream_t s);
 
 // Eq. 6 voxel-driven gradient (eq6.cu). mode 0: out = G(T); mode 1:
 // out = f - scale G(T) with scale = scale_val (* *d_scale when given)
