@@ -256,7 +256,11 @@ bp_kernel(VolGeom g, DetGeom d, const void *__restrict__ sino, int st, const flo
         if (staged) {
             const int w = iu1 - iu0 + 1, h = s1 - s0 + 1;
             const size_t src = (size_t)view * nv * nu;
-            if (st == CBCT_STORAGE_BF16)
+            if (PRESCALED && st == CBCT_STORAGE_F32) {
+                stage_patch_async<NWARPS>(patch, static_cast<const float *>(sino) + src, nu, nv, iu0, s0, w, h, hp,
+                                          wid, lane);
+                stage_async_wait();
+            } else if (st == CBCT_STORAGE_BF16)
                 stage_patch<PRESCALED, NWARPS>(patch, static_cast<const __nv_bfloat16 *>(sino) + src, g, d, view,
                                               iu0, s0, w, h, hp, wid, lane);
             else if (st == CBCT_STORAGE_F16)
@@ -305,6 +309,10 @@ bp_kernel(VolGeom g, DetGeom d, const void *__restrict__ sino, int st, const flo
                     if (hit && tlo < thi) {
                         jl = max((int)ceilf((tlo + rc.delta) * inv_drho) - 1, (int)rc.jlo);
                         jh = min((int)floorf((thi + rc.delta) * inv_drho) + 1, (int)rc.jhi);
+                        // the samples touching the group are contiguous along the line: trim
+                        // the candidate range to them
+                        while (jl <= jh && !sample_in_group(g, rc, jl, A, B)) ++jl;
+                        while (jh >= jl && !sample_in_group(g, rc, jh, A, B)) --jh;
                     }
                 }
                 const int cnt = max(jh - jl + 1, 0);

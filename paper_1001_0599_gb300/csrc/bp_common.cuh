@@ -16,6 +16,17 @@ struct Box {
 
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.f, x); }
 
+// Does sample j of the line touch the BP_G x BP_G group of columns at (A, B)?
+// Its cell (floor of the sample's voxel coordinates) must lie in
+// [A-1, A+BP_G-1] x [B-1, B+BP_G-1].
+__device__ __forceinline__ bool sample_in_group(const VolGeom &g, const RayCol &rc, int j, int A, int B)
+{
+    float fx, fy;
+    sample_xy(g, rc, j, fx, fy);
+    const int ra = (int)floorf(fx) - A, rb = (int)floorf(fy) - B;
+    return ra >= -1 && ra < BP_G && rb >= -1 && rb < BP_G;
+}
+
 // detector columns [iu0, iu1] that can see the xy box in view (c, s), and the
 // box's depth range along the central ray
 __device__ __forceinline__ void box_u_range(const DetGeom &d, float c, float s, const Box &bx,

@@ -104,16 +104,6 @@ __device__ __forceinline__ RayCol ld_raycol(const RayCol *p)
 __device__ __forceinline__ long long bs_owner(long long x, long long U, long long B) { return ((x + 1) * B - 1) / U; }
 __device__ __forceinline__ long long bs_start(long long b, long long U, long long B) { return b * U / B; }
 
-// Does sample j of the line touch the 4 x 4 group at (A, B)? Its cell
-// (floor of the sample's voxel coordinates) must lie in [A-1, A+3] x [B-1, B+3].
-__device__ __forceinline__ bool bs_in_group(const VolGeom &g, const RayCol &rc, int j, int A, int B)
-{
-    float fx, fy;
-    sample_xy(g, rc, j, fx, fy);
-    const int ra = (int)floorf(fx) - A, rb = (int)floorf(fy) - B;
-    return ra >= -1 && ra < BP_G && rb >= -1 && rb < BP_G;
-}
-
 // z tent sum of one sample for one voxel: the sum over the W rows from
 // r0 = ceil(q - m) of max(0, 1 - sc |r - q|) R_r, q the row whose sample
 // height is the voxel's centre and R the patch column starting at index col.
@@ -332,8 +322,8 @@ bs_kernel(const BsArgs a)
                             jh = min((int)floorf((thi + rc.delta) * inv_drho) + 1, (int)rc.jhi);
                             // the samples touching the group are contiguous along the line:
                             // trim the candidate range to them
-                            while (jl <= jh && !bs_in_group(g, rc, jl, A, B)) ++jl;
-                            while (jh >= jl && !bs_in_group(g, rc, jh, A, B)) --jh;
+                            while (jl <= jh && !sample_in_group(g, rc, jl, A, B)) ++jl;
+                            while (jh >= jl && !sample_in_group(g, rc, jh, A, B)) --jh;
                         }
                     }
                     const int cnt = max(jh - jl + 1, 0);

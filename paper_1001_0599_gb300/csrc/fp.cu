@@ -275,6 +275,75 @@ __device__ __forceinline__ float sheet_epilogue(const T *__restrict__ y, T *__re
     return r2;
 }
 
+constexpr float FS_ROUND = 12582912.f;     // 1.5 * 2^23: x + FS_ROUND rounds x to an integer
+constexpr int FS_ROUND_BITS = 0x4B400000;  // bit pattern of FS_ROUND
+
+// Every row k in LIVE walks the chunk's samples: the row's height at sample jj
+// in voxel units, zeta = cz + rho_jj tz_k, splits into the voxel c0 = floor
+// (a round-down add against 1.5 * 2^23, on the FMA and integer pipes) and the
+// weight of c0 + 1; the sheet row is read at c0 and c0 + 1 (clamped into its
+// zero pads).
+template <int RT, unsigned LIVE>
+__device__ __forceinline__ void sheet_walk(const float *H, int hs, const float *s_rho, int nj, const float (&tz)[RT],
+                                           float cz, int nz, float (&acc)[RT])
+{
+#pragma unroll 4
+    for (int jj = 0; jj < nj; ++jj) {
+        const float rho = s_rho[jj];
+        const int row = jj * hs + FS_PAD;
+#pragma unroll
+        for (int k = 0; k < RT; k++) {
+            if (!((LIVE >> k) & 1u)) continue;
+            const float zeta = __fmaf_rn(rho, tz[k], cz);
+            const float tb = __fadd_rd(zeta, FS_ROUND);   // FS_ROUND + floor(zeta)
+            const float c0f = tb - FS_ROUND;
+            const int c0 = clampi(__float_as_int(tb) - FS_ROUND_BITS, -2, nz);
+            const float wz1 = zeta - c0f;
+            const float h0 = H[row + c0], h1 = H[row + c0 + 1];
+            acc[k] += h0 + wz1 * (h1 - h0);
+        }
+    }
+}
+
+// the row walk specialised for the live set of bands (all 2^RT sets for up
+// to three rows per thread; a runtime test per band beyond that)
+template <int RT>
+__device__ __forceinline__ void sheet_walk_bands(unsigned live, const float *H, int hs, const float *s_rho, int nj,
+                                                 const float (&tz)[RT], float cz, int nz, float (&acc)[RT])
+{
+    if constexpr (RT <= 3) {
+        switch (live) {
+        case 1: sheet_walk<RT, 1>(H, hs, s_rho, nj, tz, cz, nz, acc); break;
+        case 2: sheet_walk<RT, 2>(H, hs, s_rho, nj, tz, cz, nz, acc); break;
+        case 3: sheet_walk<RT, 3>(H, hs, s_rho, nj, tz, cz, nz, acc); break;
+        case 4: sheet_walk<RT, 4>(H, hs, s_rho, nj, tz, cz, nz, acc); break;
+        case 5: sheet_walk<RT, 5>(H, hs, s_rho, nj, tz, cz, nz, acc); break;
+        case 6: sheet_walk<RT, 6>(H, hs, s_rho, nj, tz, cz, nz, acc); break;
+        case 7: sheet_walk<RT, 7>(H, hs, s_rho, nj, tz, cz, nz, acc); break;
+        default: break;
+        }
+    } else {
+        // tall detectors: one specialisation per band would multiply the code; walk
+        // every band, testing liveness per sample
+#pragma unroll 2
+        for (int jj = 0; jj < nj; ++jj) {
+            const float rho = s_rho[jj];
+            const int row = jj * hs + FS_PAD;
+#pragma unroll
+            for (int k = 0; k < RT; k++) {
+                if (!((live >> k) & 1u)) continue;
+                const float zeta = __fmaf_rn(rho, tz[k], cz);
+                const float tb = __fadd_rd(zeta, FS_ROUND);
+                const float c0f = tb - FS_ROUND;
+                const int c0 = clampi(__float_as_int(tb) - FS_ROUND_BITS, -2, nz);
+                const float wz1 = zeta - c0f;
+                const float h0 = H[row + c0], h1 = H[row + c0 + 1];
+                acc[k] += h0 + wz1 * (h1 - h0);
+            }
+        }
+    }
+}
+
 // register budgets: 64 for up to 3 rows per thread (8 blocks of 128 threads
 // per SM; deep volumes are limited by the sheet's shared memory first), and
 // enough for 4 or 8 rows to avoid local-memory spills
@@ -368,8 +437,10 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *
             build_sheet(H, hs, nz, static_cast<const float *>(vol), s_o, s_w, nj, clo, chi, warp, lane);
         __syncthreads();
         // 32-row bands whose rows stay outside the volume over the whole chunk
-        // (rows above the top or below the bottom for every sample) are skipped
-        bool band[RT];
+        // (rows above the top or below the bottom for every sample) are skipped;
+        // the set of live bands is warp-uniform, so the row walk is specialised
+        // for it once per chunk instead of testing every band at every sample
+        unsigned live = 0;
         {
             const float ra = s_rho[0], rb = s_rho[nj - 1];
 #pragma unroll
@@ -378,24 +449,10 @@ fp_sheet_kernel(VolGeom g, DetGeom d, const void *__restrict__ vol, const void *
                 const float z1 = __fmaf_rn(ra, t_lo, g.cz), z2 = __fmaf_rn(rb, t_lo, g.cz);
                 const float z3 = __fmaf_rn(ra, t_hi, g.cz), z4 = __fmaf_rn(rb, t_hi, g.cz);
                 const float zlo = fminf(fminf(z1, z2), fminf(z3, z4)), zhi = fmaxf(fmaxf(z1, z2), fmaxf(z3, z4));
-                band[k] = !(zhi < -1.f || zlo >= (float)nz);
+                if (!(zhi < -1.f || zlo >= (float)nz)) live |= 1u << k;
             }
         }
-#pragma unroll 4
-        for (int jj = 0; jj < nj; ++jj) {
-            const float rho = s_rho[jj];
-            const float *Hr = H + jj * hs + FS_PAD;
-#pragma unroll
-            for (int k = 0; k < RT; k++) {
-                if (!band[k]) continue;
-                const float zeta = __fmaf_rn(rho, tz[k], g.cz);
-                const float c0f = floorf(zeta);
-                const int c0 = clampi((int)c0f, -2, nz);
-                const float wz1 = zeta - c0f;
-                const float h0 = Hr[c0], h1 = Hr[c0 + 1];
-                acc[k] += h0 + wz1 * (h1 - h0);
-            }
-        }
+        sheet_walk_bands<RT>(live, H, hs, s_rho, nj, tz, g.cz, nz, acc);
         __syncthreads();
     }
 
