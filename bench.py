@@ -1,22 +1,26 @@
 #!/usr/bin/env python
 """Benchmark: TV-regularised cone-beam CT reconstruction (Algorithm A1 with the
-coarse-to-fine multigrid schedule) at paper scale on GB300.
+coarse-to-fine multigrid schedule) on GB300.
 
-One step = one full reconstruction of the paper-scale workload: a
-256x256x128 volume at 1 mm, 40 views over 360 degrees on a 512x384 detector
-at 0.78 mm (SAD 1000 mm, SDD 1500 mm), a seeded head-and-neck-like ellipsoid
-phantom with Poisson noise at 5e4 photons per ray, 3 multigrid levels
-(64 -> 128 -> 256 in-plane), 40/30/30 FBS iterations, step 1/L from 20 power
-iterations on the coarsest level and 4 per finer level started from the
-prolongated eigenvector of the previous level, lambda 0.05. The metric is
-seconds per reconstruction
-(lower is better); with N GPUs every rank reconstructs its own scan (weak
-scaling, no data-path collective) and the value is the job's time per scan.
+One step = one full reconstruction of the cubic workload (default): a 256^3
+volume at 1 mm, 40 views over 360 degrees on a 512x384 detector at 0.78 mm
+(SAD 1000 mm, SDD 1500 mm), a seeded head-and-neck-like ellipsoid phantom with
+Poisson noise at 5e4 photons per ray, 3 multigrid levels (64 -> 128 -> 256
+per axis), 40/30/30 FBS iterations, step 1/L from 20 power iterations on the
+coarsest level and 4 per finer level started from the prolongated
+eigenvector of the previous level, lambda 0.05. --workload paper takes the
+paper-scale 256x256x128 volume instead. The metric is seconds per
+reconstruction (lower is better); with N GPUs every rank reconstructs its own
+scan (weak scaling, no data-path collective) and the value is the job's time
+per scan. The same line carries the projector and transpose against HBM and
+a serving block (latency percentiles and throughput of a stream of mixed
+scans), measured after the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle on this machine's host cores (a
-bounded sample, scaled to one reconstruction).
+--impl reference times the FP64 CPU oracle on this machine's host cores: per
+step, a bounded sample of per-operation costs, multiplied by the operation
+counts of one reconstruction.
 """
 from __future__ import annotations
 
@@ -32,7 +36,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP32_LANES_PER_SM = 128
-METRIC = "recon sec at 256x256x128 x 40 views (paper-scale workload)"
+METRIC = "recon sec at 256^3x40 views; projector/backproj GB/s vs HBM; serve p50/p99"
+PAPER_METRIC = "recon sec at 256x256x128 x 40 views (paper-scale workload)"
 WORKLOAD = ("paper-scale: 256x256x128 voxels @1 mm, 40 views/360 deg, 512x384 detector @0.78 mm, "
             "SAD 1000 / SDD 1500 mm, head-and-neck-like ellipsoid phantom, Poisson 5e4 photons/ray, "
             "3-level multigrid, 40/30/30 FBS iterations, tau = 1/L (20 power iterations per level), "
@@ -58,18 +63,26 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp16"],
                     help="storage type of the sinograms and of the projector's volume copy "
                          "(FP32 arithmetic throughout)")
-    ap.add_argument("--workload", default="paper", choices=["paper", "lowdose", "cube40"],
-                    help="paper: 256x256x128, 40 views; lowdose: 256^3, 360 views, 1e4 photons; "
-                         "cube40: 256^3, 40 views")
+    ap.add_argument("--workload", default="cube40", choices=["paper", "lowdose", "cube40"],
+                    help="cube40: 256^3, 40 views (default); paper: 256x256x128, 40 views; "
+                         "lowdose: 256^3, 360 views, 1e4 photons")
+    ap.add_argument("--schedule", default=None,
+                    help="reference arm: JSON schedule (accepted ROF steps and reductions per iteration) to "
+                         "scale the oracle's unit costs by; default: the oracle's own, oracle/schedule_<workload>.json")
+    ap.add_argument("--prof-steps", type=int, default=1,
+                    help="untimed steps after the timed region with per-launch CUDA events (per-kernel figures)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving block of the default line")
     ap.add_argument("--level", type=int, default=0,
                     help="one-iteration mode: multigrid level (0 = finest)")
     ap.add_argument("--mode", default="recon", choices=["recon", "one-iteration", "serve"],
                     help="one-iteration: each step is one FBS iteration on the finest grid with a "
                          "given step (per-kernel timing and profiler captures); serve: a stream of "
                          "mixed scans through the serving runtime (latency percentiles, throughput)")
-    ap.add_argument("--serve-scans", type=int, default=64, help="serve mode: scans in the stream")
-    ap.add_argument("--serve-loads", default="0.5,0.8,1.0",
-                    help="serve mode: arrival rates as fractions of the sequential capacity")
+    ap.add_argument("--serve-scans", type=int, default=None,
+                    help="scans in the serving stream (serve mode: 64; the default line's serve block: 32)")
+    ap.add_argument("--serve-loads", default=None,
+                    help="arrival rates as fractions of the sequential capacity (serve mode: 0.5,0.8,1.0; "
+                         "the default line's serve block: 0.8,1.0)")
     return ap.parse_args()
 
 
@@ -130,38 +143,96 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
-def oracle_sample(wl, y, power_fine: int = 4):
-    """Seconds per reconstruction of the FP64 oracle, from a bounded sample:
-    P and P^T over a subset of views and one ROF solve at every multigrid
-    level, scaled by the schedule's operation counts."""
+def oracle_units(wl):
+    """Per-operation seconds of the FP64 oracle on every multigrid level of a
+    workload, from a bounded sample: P over one view; P^T over one and two
+    views (a per-call part -- the private per-thread volumes and their
+    fixed-order sum -- plus a per-view part); and the ROF solve's per-call
+    part, its cost per accepted step (gradient, trial, update) and per
+    further trial (one energy evaluation and update)."""
     import numpy as np
     from oracle import oracle as orc
     g = orc.Geometry.from_workload(wl)
     levels = len(wl.iters)
-    t_total = 0.0
     rng = np.random.default_rng(0)
-    parts = []
+    tv = orc.TVParams(eps_tv=1e-5)
+    out = []
     for lev in range(levels):
         gl = g.coarse(2 ** (levels - 1 - lev)) if lev < levels - 1 else g
-        nsub = 1
-        sub = orc.Geometry(gl.nx, gl.ny, gl.nz, gl.dx, gl.dy, gl.dz, gl.nu, gl.nv, gl.du, gl.dv, gl.sad, gl.sdd,
-                           gl.angles[:nsub].copy(), gl.step_ratio)
+
+        def sub(k):
+            return orc.Geometry(gl.nx, gl.ny, gl.nz, gl.dx, gl.dy, gl.dz, gl.nu, gl.nv, gl.du, gl.dv, gl.sad,
+                                gl.sdd, gl.angles[:k].copy(), gl.step_ratio)
+
         f = rng.random(gl.vol_shape) * 0.02
+        s1, s2 = sub(1), sub(2)
         t0 = time.perf_counter()
-        p = orc.forward_project(sub, f)
-        t1 = time.perf_counter()
-        orc.back_project(sub, p)
-        t2 = time.perf_counter()
+        p1 = orc.forward_project(s1, f)
+        t_p = time.perf_counter() - t0
+        p2 = orc.forward_project(s2, f)
+        t0 = time.perf_counter()
+        orc.back_project(s1, p1)
+        t_b1 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        orc.back_project(s2, p2)
+        t_b2 = time.perf_counter() - t0
+        bt_view = max(t_b2 - t_b1, 0.0)
         gaux = f + 0.001 * rng.standard_normal(gl.vol_shape)
-        orc.rof_solve(gl, gaux, wl.lam, 1e-5, orc.TVParams(eps_tv=1e-5))
-        t3 = time.perf_counter()
-        scale = gl.n_views / nsub
-        tp, tpt, trof = (t1 - t0) * scale, (t2 - t1) * scale, t3 - t2
-        n_fbs = wl.iters[lev]
-        n_pow = 20 if lev == 0 or power_fine <= 0 else power_fine
-        t_total += n_fbs * (tp + tpt + trof) + n_pow * (tp + tpt)
-        parts.append(f"level {lev}: P,P^T on {nsub}/{gl.n_views} views x{scale:.0f}, one ROF solve")
-    return t_total, "; ".join(parts)
+        t0 = time.perf_counter()
+        orc.rof_solve(gl, gaux, wl.lam, 1e-5, tv, replay=[0])
+        t_r1 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        orc.rof_solve(gl, gaux, wl.lam, 1e-5, tv, replay=[0, 0])
+        t_r2 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        orc.rof_energy(gl, f, gaux, wl.lam, 1e-5, 1e-5)
+        t_e = time.perf_counter() - t0
+        step = max(t_r2 - t_r1, 0.0)
+        out.append({"level": lev, "views": gl.n_views, "p_view": t_p, "pt_call": max(t_b1 - bt_view, 0.0),
+                    "pt_view": bt_view, "rof_call": max(t_r1 - step, 0.0), "rof_step": step, "rof_trial": t_e})
+    return out
+
+
+def oracle_model_seconds(units, schedule):
+    """One oracle reconstruction from the unit costs and a schedule: per level,
+    its power iterations (P and P^T each) and its FBS iterations (P, P^T and
+    one ROF solve with that iteration's accepted steps and step reductions)."""
+    total = 0.0
+    for u, lev in zip(units, schedule["levels"]):
+        pp = u["p_view"] * u["views"] + u["pt_call"] + u["pt_view"] * u["views"]
+        total += lev["power"] * pp
+        for it in lev["fbs"]:
+            total += pp + u["rof_call"] + it["n_inner"] * u["rof_step"] + it["backtracks"] * u["rof_trial"]
+    return total
+
+
+def schedule_from_stats(st, wl, power_fine: int):
+    """The reconstruction's own schedule (accepted steps and reductions of every
+    ROF solve) from the library's statistics."""
+    levels = [{"power": 20 if lev == 0 or power_fine <= 0 else power_fine, "fbs": []} for lev in range(len(wl.iters))]
+    for k in range(int(st.n_iters)):
+        it = st.iters[k]
+        levels[int(it.level)]["fbs"].append({"n_inner": int(it.n_inner), "backtracks": int(it.backtracks)})
+    return {"levels": levels, "source": "this run's reconstruction statistics"}
+
+
+def schedule_from_oracle(name: str, power_fine: int):
+    """The oracle's own schedule for the workload (oracle/make_schedule.py)."""
+    path = os.path.join(ROOT, "oracle", f"schedule_{name}.json")
+    with open(path) as fh:
+        d = json.load(fh)
+    levels = [{"power": d["power_iters"] if lev == 0 or power_fine <= 0 else power_fine, "fbs": lv["fbs"]}
+              for lev, lv in enumerate(d["levels"])]
+    return {"levels": levels, "source": f"oracle/schedule_{name}.json (the oracle's full reconstruction)"}
+
+
+def oracle_sample(wl, schedule):
+    """Seconds per oracle reconstruction: unit costs timed now, multiplied by
+    the schedule's operation counts."""
+    units = oracle_units(wl)
+    desc = ("per level: P on 1 view, P^T on 1 and 2 views (per-call and per-view parts), ROF per-call, "
+            "per-step and per-trial costs; times the schedule's counts from " + schedule["source"])
+    return oracle_model_seconds(units, schedule), desc, units
 
 
 def rank_noise_seed(base_seed: int, rank: int) -> int:
@@ -201,34 +272,42 @@ def workload_description(args):
         f"warm-started from the prolongated eigenvector)")
     if args.gradient == "eq6":
         workload += "; Step 1 gradient from the paper's closed form (Eq. 6) instead of the matched transpose"
-    metric = METRIC
+    metric = PAPER_METRIC
     if args.workload == "lowdose":
         workload = workload.replace("paper-scale: 256x256x128 voxels", "low-dose: 256x256x256 voxels").replace(
             "40 views/360 deg", "360 views/360 deg").replace("Poisson 5e4", "Poisson 1e4")
         metric = "recon sec at 256^3 x 360 views (low-dose workload)"
     if args.workload == "cube40":
         workload = workload.replace("paper-scale: 256x256x128 voxels", "cubic: 256x256x256 voxels")
-        metric = "recon sec at 256^3 x 40 views"
+        metric = METRIC
     if args.storage != "f32":
         workload += (f"; measured sinogram, residual and the projector's volume copy stored as {args.storage} "
                      "(FP32 arithmetic, FP64 sums)")
     return workload, metric
 
 
-def cpu_baseline_subprocess():
-    """The oracle's bounded sample timed in a fresh process (this one holds a
-    CUDA context and PyTorch's thread pools), exactly as the reference arm
-    times it: one untimed warm-up projection, then the sample."""
+def cpu_baseline_subprocess(args, schedule):
+    """The oracle sample timed in a fresh process (this one holds a CUDA context
+    and PyTorch's thread pools), exactly as the reference arm times it, with
+    this run's schedule."""
+    import tempfile
     env = {k: v for k, v in os.environ.items()
            if k not in ("RANK", "LOCAL_RANK", "WORLD_SIZE", "MASTER_ADDR", "MASTER_PORT")}
-    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], capture_output=True, text=True, env=env, cwd=ROOT)
+    with tempfile.NamedTemporaryFile("w", suffix=".json", delete=False) as fh:
+        json.dump(schedule, fh)
+        path = fh.name
+    try:
+        res = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1",
+                              "--warmup", "0", "--workload", args.workload, "--power-fine", str(args.power_fine),
+                              "--schedule", path], capture_output=True, text=True, env=env, cwd=ROOT)
+    finally:
+        os.unlink(path)
     lines = [l for l in res.stdout.splitlines() if l.startswith("{")]
     if res.returncode != 0 or not lines:
         return {"value": None, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
                 "sample": "failed: " + (res.stderr.strip().splitlines() or ["no output"])[-1]}
     ref = json.loads(lines[-1])["cpu_baseline"]
-    ref["sample"] += " (scaled to one reconstruction; timed in a separate process)"
+    ref["sample"] += " (timed in a separate process)"
     return ref
 
 
@@ -245,24 +324,36 @@ def run_reference(args, rank, world):
     from oracle import oracle as orc
     from paper_1001_0599_gb300 import synthetic
     orc.build()
-    wl = synthetic.workload("paper")
-    _, y = synthetic.make_problem(wl)
+    wl = synthetic.workload(args.workload)
+    if args.schedule:
+        with open(args.schedule) as fh:
+            schedule = json.load(fh)
+    else:
+        schedule = schedule_from_oracle(args.workload, args.power_fine)
     oracle_sample_warm(wl)
     times = []
-    sample = ""
+    sample, units = "", None
     for i in range(args.warmup + args.steps):
-        t, sample = oracle_sample(wl, y, args.power_fine)
+        t, sample, units = oracle_sample(wl, schedule)
         if i >= args.warmup:
             times.append(t)
     v = statistics.mean(times)
-    line = {"impl": "reference", "metric": workload_description(args)[1], "value": v, "unit": "s", "n_gpus": args.gpus,
+    workload, metric = workload_description(args)
+    line = {"impl": "reference", "metric": metric, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_description(args)[0], "parallelism": "host cores (OpenMP)"},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "config": run_config(workload), "parallelism": "host cores (OpenMP)",
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": sample,
+                             "units": units},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_config(workload: str):
+    """The run's configuration, the same for both arms."""
+    return {"workload": workload, "l2": "flushed (512 MB write) before every timed step",
+            "reductions": "FP64 across blocks, compensated FP32 within"}
 
 
 # ---------------------------------------------------------------------------
@@ -329,7 +420,10 @@ def main():
         uuid = None
     sampler = ClockSampler(uuid)
     cbct.cbct_profile_reset()
-    cbct.cbct_profile_enable(True)
+    # the reconstruction's timed steps run without the per-launch profiling
+    # events; its per-kernel figures come from separate steps afterwards
+    profile_timed = args.mode == "one-iteration"
+    cbct.cbct_profile_enable(profile_timed)
     n0 = cbct.cbct_launch_count()
     if dist:
         dist.barrier()
@@ -345,12 +439,24 @@ def main():
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        cbct.cbct_profile_collect()
+        if profile_timed:
+            cbct.cbct_profile_collect()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    launches = cbct.cbct_launch_count() - n0 - 0
+    launches = cbct.cbct_launch_count() - n0
+    prof_steps = args.steps
+    if not profile_timed:
+        # per-kernel figures (roofline, bandwidth, breakdown): untimed steps with
+        # CUDA events around every launch, L2 flushed as in the timed steps
+        prof_steps = max(args.prof_steps, 1)
+        cbct.cbct_profile_enable(True)
+        for _ in range(prof_steps):
+            flush.zero_()
+            step()
+            cbct.cbct_profile_collect()
+        torch.cuda.synchronize()
     cbct.cbct_profile_enable(False)
     prof = cbct.cbct_profile_query()
     prof_levels = {lev: cbct.cbct_profile_query_level(lev) for lev in range(len(wl.iters))}
@@ -423,26 +529,36 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32 ({args.storage} storage)",
             "data": "synthetic",
-            "config": {"workload": workload, "l2": "flushed (512 MB write) before every timed step",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "reductions": "FP64 across blocks, compensated FP32 within"},
+            "config": run_config(workload),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "clocks": clocks, "gpu_launches": int(launches), "roofline": roof,
             "projector_bandwidth": bandwidth,
             "e2e": e2e,
-            "kernels": {k: {"launches": n // max(args.steps, 1), "ms_per_step": ms / max(args.steps, 1)}
+            "kernels": {k: {"launches": n // prof_steps, "ms_per_step": ms / prof_steps}
                         for k, (n, ms) in prof.items() if n},
+            "kernels_note": f"from {prof_steps} untimed step(s) after the timed region with CUDA events around "
+                            "every launch; the timed steps ran without them",
             "storage_error": storage_error,
             "quality": {"rel_error_vs_phantom": rel_err, "correlation": corr, "flags": int(st.flags),
                         "status": int(st.status), "taus": [float(st.tau[i]) for i in range(3)]},
             "paper_context": PAPER_CONTEXT,
             "peaks_source": peaks.get("_source")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_subprocess()
+        line["cpu_baseline"] = cpu_baseline_subprocess(args, schedule_from_stats(st, wl, args.power_fine))
+    if rank == 0 and world == 1 and not args.no_serve and args.storage == "f32":
+        del ws, d_y, vol, flush
+        torch.cuda.empty_cache()
+        line["serve"] = serve_summary(serve_measure(args.serve_scans or 32,
+                                                    parse_loads(args.serve_loads or "0.8,1.0"), "f32", local))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def parse_loads(text: str):
+    return [float(x) for x in text.split(",") if x]
 
 
 # ---------------------------------------------------------------------------
@@ -473,14 +589,37 @@ def fifo_latencies(arrivals, service):
 
 
 def serve_bench(args, rank, world, local):
-    """Serving benchmark (no counterpart in the paper): --serve-scans scans
-    drawn from 4 grids x 2 detectors x 4 view counts, each reconstructed with
-    50 FBS-TV iterations (3-level multigrid 20/15/15), arriving as a Poisson
-    stream at several fractions of the sequential capacity. The sequential
-    system processes one scan at a time through cbct_reconstruct_host (copy
-    in, reconstruct, copy out, wait); the server overlaps copies with compute
-    and replays captured graphs. Outputs are checked bit-identical between
-    the two, so the RMS error is equal by construction."""
+    """Serving benchmark (--mode serve; no counterpart in the paper): the full
+    table of serve_measure on --serve-scans scans (default 64) at loads
+    0.5, 0.8 and 1.0 of the sequential capacity."""
+    res = serve_measure(args.serve_scans or 64, parse_loads(args.serve_loads or "0.5,0.8,1.0"), args.storage,
+                        local)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    return 0
+
+
+def serve_summary(res):
+    """The serving figures the default line carries."""
+    keep = ("p50_s", "p99_s", "scans_per_min", "sequential_p50_s", "sequential_p99_s")
+    return {"metric": "scan latency p50/p99 (s) and scans/min of a mixed stream, beside the sequential plain "
+                      "FP32 path on the same GPU",
+            "scans": res["scans"], "loads": [{"load": r["load"], **{k: r[k] for k in keep}} for r in res["loads"]],
+            "sequential_scans_per_min": res["sequential"]["scans_per_min"],
+            "server_burst_scans_per_min": res["server_burst"]["scans_per_min"],
+            "bit_identical_to_sequential": res["bit_identical_to_sequential"],
+            "workload": res["config"]["workload"], "clocks": res["clocks"]}
+
+
+def serve_measure(n_scans, loads, storage, local):
+    """A stream of n_scans scans drawn from 4 grids x 2 detectors x 4 view
+    counts, each reconstructed with 50 FBS-TV iterations (3-level multigrid
+    20/15/15), arriving as a Poisson stream at the given fractions of the
+    sequential capacity. The sequential system processes one scan at a time
+    through cbct_reconstruct_host (copy in, reconstruct, copy out, wait); the
+    server overlaps copies with compute and replays captured graphs. Outputs
+    are checked bit-identical between the two, so the RMS error is equal by
+    construction."""
     import hashlib
 
     import numpy as np
@@ -491,13 +630,13 @@ def serve_bench(args, rank, world, local):
     from paper_1001_0599_gb300 import cbct, synthetic
 
     torch.cuda.set_device(local)
-    stream = serve_stream(args.serve_scans)
+    stream = serve_stream(n_scans)
     tv = cbct.TvParams.paper(eps_tv=1e-5)
     params = cbct.make_recon_params(0.05, SERVE_ITERS, tv, power_iters=20, clamp=True, power_iters_fine=4)
     # the service may store sinograms and the projector's volume copy at reduced
     # precision; the sequential baseline is plain FP32 storage
     sparams = cbct.make_recon_params(0.05, SERVE_ITERS, tv, power_iters=20, clamp=True, power_iters_fine=4,
-                                     storage=args.storage)
+                                     storage=storage)
     geoms, truths, scans = {}, {}, []
     for i, (gi, di, vi) in enumerate(stream):
         nx, ny, nz, dx, dy, dz = SERVE_GRIDS[gi]
@@ -559,7 +698,7 @@ def serve_bench(args, rank, world, local):
         srv.wait(t)
     identical = True
     sampler.start()
-    for load in [float(x) for x in args.serve_loads.split(",") if x]:
+    for load in loads:
         rate = load * capacity
         arr = np.cumsum(np.random.default_rng(10).exponential(1.0 / rate, len(scans)))
         arr -= arr[0]
@@ -601,7 +740,7 @@ def serve_bench(args, rank, world, local):
     line = {"metric": "serving: scan latency p50/p99 (s) and scans/min, mixed 64-scan stream",
             "mode": "serve", "value": results[-1]["p99_s"] if results else None, "unit": "s (p99 at the highest load)",
             "higher_is_better": False, "n_gpus": 1,
-            "dtype": "f32" if args.storage == "f32" else f"f32 ({args.storage} storage)", "data": "synthetic",
+            "dtype": "f32" if storage == "f32" else f"f32 ({storage} storage)", "data": "synthetic",
             "config": {"workload": f"{len(scans)} scans; grids {SERVE_GRIDS}; detectors {SERVE_DETECTORS}; "
                                    f"views {SERVE_VIEWS}; 50 FBS-TV iterations (multigrid 20/15/15), "
                                    "lambda 0.05, Poisson 5e4 photons; stream seed 10",
@@ -609,8 +748,8 @@ def serve_bench(args, rank, world, local):
             "sequential": {"scans_per_min": 60.0 * capacity, "total_s": seq_total,
                            "mean_service_s": float(np.mean(service))},
             "server_burst": {"scans_per_min": 60.0 * len(scans) / burst, "total_s": burst},
-            "loads": results, "storage": args.storage,
-            "bit_identical_to_sequential": bool(identical) if args.storage == "f32" else None,
+            "loads": results, "storage": storage, "scans": len(scans),
+            "bit_identical_to_sequential": bool(identical) if storage == "f32" else None,
             "rms_error_vs_phantom": {"sequential_f32": float(np.mean(rms)), "server": float(np.mean(rms_srv)),
                                      "max_rel_diff_per_scan": float(max(abs(a - b) / b for a, b in
                                                                         zip(rms_srv, rms)))},
@@ -618,9 +757,7 @@ def serve_bench(args, rank, world, local):
                        "graph_failures": int(info.graph_failures), "evictions": int(info.evictions),
                        "peak_arena_gb": info.peak_bytes_in_use / 1e9, "arena_gb": info.arena_bytes / 1e9},
             "clocks": clocks}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def measured_peaks():
@@ -634,7 +771,8 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "_source": "fallback"}
 
 
-KERNEL_SOURCES = {"back_project_step": ["bp.cu"], "back_project": ["bp.cu"],
+KERNEL_SOURCES = {"back_project_step": ["bp.cu", "bps.cu", "bp_common.cuh"],
+                  "back_project": ["bp.cu", "bps.cu", "bp_common.cuh"],
                   "forward_residual": ["fp.cu"], "forward_project": ["fp.cu"]}
 
 

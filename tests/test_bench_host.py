@@ -26,7 +26,9 @@ def _args(**kw):
 
 def test_workload_descriptions(bench):
     w, m = bench.workload_description(_args())
-    assert "256x256x128" in w and "4 per finer level" in w and m == bench.METRIC
+    assert "256x256x128" in w and "4 per finer level" in w and m == bench.PAPER_METRIC
+    w, m = bench.workload_description(_args(workload="cube40"))
+    assert "256x256x256" in w and "40 views" in w and m == bench.METRIC
     w, m = bench.workload_description(_args(workload="lowdose", storage="bf16", gradient="eq6"))
     assert "256x256x256" in w and "360 views" in w and "bf16" in w and "Eq. 6" in w and "low-dose" in m
     w, _ = bench.workload_description(_args(power_fine=0))
@@ -73,3 +75,31 @@ def test_serve_stream_and_fifo_model(bench):
     assert {x[0] for x in a} <= set(range(len(bench.SERVE_GRIDS)))
     # one-at-a-time queue: the second job waits for the first
     assert bench.fifo_latencies([0.0, 0.5, 5.0], [1.0, 1.0, 1.0]) == [1.0, 1.5, 1.0]
+
+
+def test_oracle_model_counts_every_operation_once(bench):
+    # two levels with made-up unit costs: P^T's per-call part is paid once per
+    # call, its per-view part per view; ROF per call, per accepted step, per reduction
+    units = [{"views": 40, "p_view": 0.1, "pt_call": 1.0, "pt_view": 0.2, "rof_call": 0.5, "rof_step": 0.3,
+              "rof_trial": 0.05},
+             {"views": 40, "p_view": 0.2, "pt_call": 2.0, "pt_view": 0.4, "rof_call": 1.0, "rof_step": 0.6,
+              "rof_trial": 0.1}]
+    sched = {"levels": [{"power": 20, "fbs": [{"n_inner": 3, "backtracks": 2}]},
+                        {"power": 4, "fbs": [{"n_inner": 1, "backtracks": 0}, {"n_inner": 2, "backtracks": 5}]}]}
+    pp0 = 0.1 * 40 + 1.0 + 0.2 * 40
+    pp1 = 0.2 * 40 + 2.0 + 0.4 * 40
+    want = 20 * pp0 + (pp0 + 0.5 + 3 * 0.3 + 2 * 0.05) + 4 * pp1 + (pp1 + 1.0 + 0.6) + (pp1 + 1.0 + 2 * 0.6 + 5 * 0.1)
+    assert bench.oracle_model_seconds(units, sched) == pytest.approx(want)
+
+
+def test_schedule_from_reconstruction_statistics(bench):
+    from types import SimpleNamespace
+    from paper_1001_0599_gb300 import synthetic
+    wl = synthetic.workload("paper")
+    its = [SimpleNamespace(level=0, n_inner=4, backtracks=1)] * 40 + \
+          [SimpleNamespace(level=1, n_inner=3, backtracks=0)] * 30 + [SimpleNamespace(level=2, n_inner=2, backtracks=2)] * 30
+    st = SimpleNamespace(n_iters=100, iters=its)
+    sched = bench.schedule_from_stats(st, wl, 4)
+    assert [lv["power"] for lv in sched["levels"]] == [20, 4, 4]
+    assert [len(lv["fbs"]) for lv in sched["levels"]] == [40, 30, 30]
+    assert sched["levels"][2]["fbs"][0] == {"n_inner": 2, "backtracks": 2}
