@@ -184,9 +184,19 @@ cbct_status cbct_residual(const cbct_geometry *geom, const float *d_vol, const f
  * nothing. The first call on each device looks up that array's device
  * address; make that first call before any stream capture. All calls share
  * the one array: calls that may overlap on the GPU (different streams, or
- * several threads) race and give wrong sums; serialise them. Geometries with
- * n_views * nu above CBCT_STATIC_MAX_PARTIALS are rejected with
- * CBCT_ERR_UNSUPPORTED. Results equal cbct_residual's. */
+ * several threads) race and give wrong sums; serialise them. The array
+ * holds one partial sum per block of the forward launch, and a geometry
+ * whose launch has more blocks than CBCT_STATIC_MAX_PARTIALS is rejected
+ * with CBCT_ERR_UNSUPPORTED. That count is n_views * nu on the sheet
+ * projector (detectors of at most 1024 rows and volumes of at most 760
+ * slices), and n_views * ceil(nu / 8) * ceil(nv / (32 r)) on the
+ * warp-per-column projector that serves every other geometry, where r is
+ * 1, 2 or 4 detector rows per lane, the largest whose rows' z span fits the
+ * kernel's 64-slice segment. The array's device address is looked up once
+ * per device and kept; a device reset (cudaDeviceReset) or any other
+ * teardown of the device's primary context invalidates it, so this call
+ * must not be used on that device afterwards in the same process.
+ * Results equal cbct_residual's. */
 #define CBCT_STATIC_MAX_PARTIALS 262144
 cbct_status cbct_residual_static(const cbct_geometry *geom, const float *d_vol, const float *d_y,
                                  float *d_r, double *d_sumsq, void *stream);
@@ -367,7 +377,9 @@ int64_t cbct_launch_count(void);
 /* Per-kernel timing with CUDA events on the launch stream: while enabled,
  * every launch is bracketed by two events; cbct_profile_collect waits for
  * them and adds their durations to per-kernel totals. Kernel ids
- * 0 .. cbct_profile_kernels()-1. Not thread-safe. */
+ * 0 .. cbct_profile_kernels()-1. Launches from several host threads are
+ * recorded safely (each thread pairs its own events); collect, query and
+ * reset while no launch is being issued. */
 cbct_status cbct_profile_enable(int on);
 cbct_status cbct_profile_collect(void);
 int cbct_profile_kernels(void);

@@ -10,6 +10,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -54,12 +56,19 @@ std::atomic<int64_t> g_launches{0};
 struct ProfSlot {
     int kernel;
     int level;     // multigrid level of the launch (0 = finest), -1 outside a reconstruction
+    bool done;     // both events recorded
     cudaEvent_t start, stop;
 };
-bool g_prof_on = false;
+std::atomic<bool> g_prof_on{false};
 thread_local bool t_quiet = false;   // threads whose launches the profiler skips
-std::vector<ProfSlot> g_pool;
+// Event pairs, reused across collections. A deque keeps references stable
+// while other threads append; g_prof_mutex guards the pool, the counters
+// and the totals, and each thread remembers the slot its open launch took,
+// so launches from several host threads pair their own events.
+std::mutex g_prof_mutex;
+std::deque<ProfSlot> g_pool;
 size_t g_pool_used = 0;
+thread_local long t_slot = -1;
 // per kernel and level slot (slot 0: outside a reconstruction, slot l + 1: level l)
 int64_t g_prof_count[K_COUNT][CBCT_MAX_LEVELS + 1] = {};
 double g_prof_ms[K_COUNT][CBCT_MAX_LEVELS + 1] = {};
@@ -73,16 +82,22 @@ namespace cbct {
 void launch_begin(int kernel, cudaStream_t s)
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (!g_prof_on || t_quiet) return;
-    if (g_pool_used == g_pool.size()) {
-        ProfSlot p{};
-        if (cudaEventCreate(&p.start) != cudaSuccess || cudaEventCreate(&p.stop) != cudaSuccess) return;
-        g_pool.push_back(p);
+    if (!g_prof_on.load(std::memory_order_relaxed) || t_quiet) return;
+    ProfSlot *p = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_prof_mutex);
+        if (g_pool_used == g_pool.size()) {
+            ProfSlot q{};
+            if (cudaEventCreate(&q.start) != cudaSuccess || cudaEventCreate(&q.stop) != cudaSuccess) return;
+            g_pool.push_back(q);
+        }
+        t_slot = (long)g_pool_used++;
+        p = &g_pool[(size_t)t_slot];
+        p->kernel = kernel;
+        p->level = t_level;
+        p->done = false;
     }
-    ProfSlot &p = g_pool[g_pool_used];
-    p.kernel = kernel;
-    p.level = t_level;
-    cudaEventRecord(p.start, s);
+    cudaEventRecord(p->start, s);
 }
 
 void note_extra_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -91,11 +106,14 @@ void set_thread_quiet(bool quiet) { t_quiet = quiet; }
 
 void launch_end(int kernel, cudaStream_t s)
 {
-    if (!g_prof_on || t_quiet) return;
-    if (g_pool_used < g_pool.size() && g_pool[g_pool_used].kernel == kernel) {
-        cudaEventRecord(g_pool[g_pool_used].stop, s);
-        g_pool_used++;
+    if (t_slot < 0) return;
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    if ((size_t)t_slot < g_pool_used && g_pool[(size_t)t_slot].kernel == kernel) {
+        ProfSlot &p = g_pool[(size_t)t_slot];
+        cudaEventRecord(p.stop, s);
+        p.done = true;
     }
+    t_slot = -1;
 }
 } // namespace cbct
 
@@ -108,6 +126,7 @@ struct LevelData {
     RayCol *d_cols;
     double drho;
     double dx, dy, dz;
+    Eq6Geom eq6;
 };
 
 struct cbct_geometry {
@@ -117,9 +136,17 @@ struct cbct_geometry {
     int device;
     DetGeom det;
     float2 *d_views;
+    float4 *d_views_df;        // (cos, sin) as double-float pairs (Eq. 6 kernel)
     int n_levels;
     LevelData lev[CBCT_MAX_LEVELS];
 };
+
+// a double as a double-float pair (hi = nearest float, lo = the remainder)
+static DF df_of(double x)
+{
+    const float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+}
 
 static double support_radius(int nx, int ny, double dx, double dy)
 {
@@ -231,6 +258,7 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
         for (auto &L : G->lev)
             if (L.d_cols) cudaFree(L.d_cols);
         if (G->d_views) cudaFree(G->d_views);
+        if (G->d_views_df) cudaFree(G->d_views_df);
         delete G;
     };
     std::vector<float2> views(d.n_views);
@@ -240,6 +268,20 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
         return fail(CBCT_ERR_OUT_OF_MEMORY, "cudaMalloc of the view table failed");
     }
     if (cudaMemcpy(G->d_views, views.data(), sizeof(float2) * d.n_views, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cleanup();
+        return fail(CBCT_ERR_CUDA, "copy of the view table failed");
+    }
+    std::vector<float4> views_df(d.n_views);
+    for (int k = 0; k < d.n_views; k++) {
+        const DF c = df_of(std::cos(d.angles[k])), sn = df_of(std::sin(d.angles[k]));
+        views_df[k] = make_float4(c.hi, c.lo, sn.hi, sn.lo);
+    }
+    if (cudaMalloc(&G->d_views_df, sizeof(float4) * d.n_views) != cudaSuccess) {
+        cleanup();
+        return fail(CBCT_ERR_OUT_OF_MEMORY, "cudaMalloc of the view table failed");
+    }
+    if (cudaMemcpy(G->d_views_df, views_df.data(), sizeof(float4) * d.n_views, cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
         cleanup();
         return fail(CBCT_ERR_CUDA, "copy of the view table failed");
     }
@@ -309,6 +351,20 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
         L.dx = dx;
         L.dy = dy;
         L.dz = dz;
+        Eq6Geom &e = L.eq6;
+        e.dx = df_of(dx);
+        e.dy = df_of(dy);
+        e.dz = df_of(dz);
+        e.cx = v.cx;
+        e.cy = v.cy;
+        e.cz = v.cz;
+        e.sad = df_of(d.sad);
+        e.ku = df_of(d.sdd / d.du);
+        e.kv = df_of(d.sdd / d.dv);
+        e.cu = det.cu;
+        e.cv = det.cv;
+        e.two_l0sq = (float)(2.0 * d.sdd * d.sdd);
+        e.views = G->d_views_df;
         L.ok = true;
         G->n_levels = l + 1;
     }
@@ -325,6 +381,7 @@ extern "C" void cbct_geometry_destroy(cbct_geometry *G)
     for (auto &L : G->lev)
         if (L.d_cols) cudaFree(L.d_cols);
     if (G->d_views) cudaFree(G->d_views);
+    if (G->d_views_df) cudaFree(G->d_views_df);
     if (prev >= 0 && prev != G->device) cudaSetDevice(prev);
     delete G;
 }
@@ -555,7 +612,7 @@ extern "C" cbct_status cbct_eq6_gradient(const cbct_geometry *G, const float *d_
     CHECK(check_geom(G));
     CHECK(check_ptr(d_T, "d_T"));
     CHECK(check_ptr(d_vol, "d_vol"));
-    CUDA_TRY(launch_eq6(G->lev[0].vg, G->det, d_T, nullptr, d_vol, nullptr, 0.0, 0, (cudaStream_t)stream));
+    CUDA_TRY(launch_eq6(G->lev[0].vg, G->det, G->lev[0].eq6, d_T, nullptr, d_vol, nullptr, 0.0, 0, (cudaStream_t)stream));
     return ok();
 }
 
@@ -898,8 +955,8 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
                 // P^T T tends to (voxel volume / (2 du dv)) G(T) (Eq. 6 carries a factor 2)
                 CUDA_TRY(launch_forward(v, G->det, f, d_sino, r, nullptr, partials, 1, s));
                 CUDA_TRY(launch_e2(partials, fp_partials_count(v, G->det), inv_m, st, s));
-                const double eq6_factor = (double)v.dx * v.dy * v.dz / (2.0 * (double)G->det.du * G->det.dv);
-                CUDA_TRY(launch_eq6(v, G->det, r, f, g, &st->scale, eq6_factor, 1, s));
+                const double eq6_factor = G->lev[gl].dx * G->lev[gl].dy * G->lev[gl].dz / (2.0 * G->desc.du * G->desc.dv);
+                CUDA_TRY(launch_eq6(v, G->det, G->lev[gl].eq6, r, f, g, &st->scale, eq6_factor, 1, s));
             } else if (sto != CBCT_STORAGE_F32) {
                 // Step 1 with y, r and the projector's copy of f stored as `sto`
                 CUDA_TRY(launch_convert(f, CBCT_STORAGE_F32, fsto, sto, nvox(v), s));
@@ -988,8 +1045,10 @@ extern "C" cbct_status cbct_profile_enable(int on)
 
 extern "C" cbct_status cbct_profile_collect(void)
 {
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
     for (size_t i = 0; i < g_pool_used; i++) {
         ProfSlot &p = g_pool[i];
+        if (!p.done) continue;   // a launch that failed before its end event
         CUDA_TRY(cudaEventSynchronize(p.stop));
         float ms = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&ms, p.start, p.stop));
@@ -1008,6 +1067,7 @@ extern "C" const char *cbct_profile_name(int k) { return (k >= 0 && k < K_COUNT)
 extern "C" cbct_status cbct_profile_query(int k, int64_t *launches, double *total_ms)
 {
     if (k < 0 || k >= K_COUNT || !launches || !total_ms) return fail(CBCT_ERR_INVALID_ARG, "bad kernel id");
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
     *launches = 0;
     *total_ms = 0.0;
     for (int l = 0; l <= CBCT_MAX_LEVELS; l++) {
@@ -1021,6 +1081,7 @@ extern "C" cbct_status cbct_profile_query_level(int k, int level, int64_t *launc
 {
     if (k < 0 || k >= K_COUNT || !launches || !total_ms || level < -1 || level >= CBCT_MAX_LEVELS)
         return fail(CBCT_ERR_INVALID_ARG, "bad kernel id or level");
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
     *launches = g_prof_count[k][level + 1];
     *total_ms = g_prof_ms[k][level + 1];
     return ok();
@@ -1028,6 +1089,7 @@ extern "C" cbct_status cbct_profile_query_level(int k, int level, int64_t *launc
 
 extern "C" void cbct_profile_reset(void)
 {
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
     for (int k = 0; k < K_COUNT; k++) {
         for (int l = 0; l <= CBCT_MAX_LEVELS; l++) {
             g_prof_count[k][l] = 0;

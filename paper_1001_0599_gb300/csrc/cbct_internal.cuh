@@ -76,6 +76,19 @@ struct DF {
     float hi, lo;
 };
 
+// Geometry of the Eq. 6 kernel (eq6.cu) for one grid, derived in FP64 on
+// the host and handed over as double-float pairs where the detector
+// coordinate needs more than FP32.
+struct Eq6Geom {
+    DF dx, dy, dz;             // voxel pitch
+    float cx, cy, cz;          // (n - 1) / 2
+    DF sad;                    // source-to-axis distance
+    DF ku, kv;                 // L0 / du, L0 / dv (L0 = source-to-detector distance)
+    float cu, cv;              // (nu - 1) / 2, (nv - 1) / 2
+    float two_l0sq;            // 2 L0^2
+    const float4 *views;       // (cos hi, cos lo, sin hi, sin lo) per view
+};
+
 __device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
 
 __device__ __forceinline__ DF df_add(DF a, float b)
@@ -272,8 +285,8 @@ cudaError_t launch_bs(const VolGeom &v, const DetGeom &d, const void *sino, int 
 
 // Eq. 6 voxel-driven gradient (eq6.cu). mode 0: out = G(T); mode 1:
 // out = f - scale G(T) with scale = scale_val (* *d_scale when given)
-cudaError_t launch_eq6(const VolGeom &v, const DetGeom &d, const float *T, const float *f, float *out,
-                       const double *d_scale, double scale_val, int mode, cudaStream_t s);
+cudaError_t launch_eq6(const VolGeom &v, const DetGeom &d, const Eq6Geom &e, const float *T, const float *f,
+                       float *out, const double *d_scale, double scale_val, int mode, cudaStream_t s);
 
 // small kernels (misc.cu)
 cudaError_t launch_sum_partials(const double *partials, int n, int stride, int k, double *out,

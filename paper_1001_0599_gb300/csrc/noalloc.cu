@@ -56,8 +56,8 @@ extern "C" cbct_status cbct_residual_static(const cbct_geometry *geom, const flo
     const int n = fp_partials_count(*v, *d);
     if (n > kStaticPartials)
         return report_error(CBCT_ERR_UNSUPPORTED,
-                            "geometry needs more partial sums than the fixed array holds "
-                            "(n_views * nu must not exceed CBCT_STATIC_MAX_PARTIALS); use cbct_residual");
+                            "geometry needs more partial sums than the fixed array holds (the forward "
+                            "launch's block count must not exceed CBCT_STATIC_MAX_PARTIALS); use cbct_residual");
     double *partials = nullptr;
     cudaError_t e = static_partials(dev, &partials);
     if (e != cudaSuccess) return report_error(CBCT_ERR_CUDA, cudaGetErrorString(e));

@@ -15,6 +15,8 @@
 // 8 x 8 x 32 voxel bricks staged with a one-voxel halo in shared memory.
 #include "cbct_internal.cuh"
 
+#include <mutex>
+
 #include <cooperative_groups.h>
 
 namespace cbct {
@@ -451,19 +453,24 @@ __global__ void rof_status_kernel(DevState *st, cbct_tv_stats *tv, cbct_recon_st
     }
 }
 
-static int g_rof_blocks = 0;
+// cooperative grid size of rof_kernel (SMs x resident blocks), per device
+static std::mutex g_rof_mutex;
+static int g_rof_blocks[64] = {};
 
 int rof_grid_blocks()
 {
-    if (g_rof_blocks == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rof_kernel, TV_THREADS, 0);
-        if (per_sm < 1) per_sm = 1;
-        g_rof_blocks = sms * per_sm;
-    }
-    return g_rof_blocks;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+    std::lock_guard<std::mutex> lock(g_rof_mutex);
+    int *cached = dev < 64 ? &g_rof_blocks[dev] : nullptr;
+    if (cached && *cached) return *cached;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rof_kernel, TV_THREADS, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int n = sms * per_sm;
+    if (cached) *cached = n;
+    return n;
 }
 
 cudaError_t launch_rof(const RofArgs &a, cudaStream_t s)

@@ -58,3 +58,51 @@ def test_static_residual_rejects_oversized_geometry(lib):
         lib.cbct_residual_static(g, vol, y, r, s)
     assert err.value.status == 6
     assert "CBCT_STATIC_MAX_PARTIALS" in str(err.value)
+
+
+def _tall_detector_geometry(lib, n_views):
+    # 1100 detector rows: the warp-per-column projector, one row per lane
+    # (its rows' z span, 32 * 2.27 slices, exceeds the 64-slice segment for
+    # two), so the forward launch has n_views * ceil(8/8) * ceil(1100/32)
+    # = 35 n_views blocks, one partial sum each
+    return lib.cbct_geometry_create(8, 8, 8, 1.0, 1.0, 0.3, 8, 1100, 1.0, 1.0, 300.0, 450.0,
+                                    np.linspace(0, 2 * np.pi, n_views, endpoint=False))
+
+
+def test_static_residual_on_the_warp_per_column_projector(lib):
+    import torch
+    g = _tall_detector_geometry(lib, 6)
+    ws = lib.workspace(lib.cbct_workspace_size(g))
+    rng = np.random.default_rng(22)
+    f = f32(rng.random(g.vol_shape))
+    y = f32(rng.random(g.sino_shape))
+    r_ref = torch.empty(g.sino_shape, device="cuda")
+    s_ref = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lib.cbct_residual(g, dev(f), dev(y), r_ref, s_ref, ws)
+    r = torch.full(g.sino_shape, float("nan"), device="cuda")
+    s = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    lib.cbct_residual_static(g, dev(f), dev(y), r, s)
+    assert rel_l2(host(r), host(r_ref)) < TOL_CALL
+    assert float(s.item()) == pytest.approx(float(s_ref.item()), rel=TOL_CALL)
+
+
+def test_static_residual_limit_counts_forward_blocks(lib):
+    import torch
+    limit = 262144
+    # 35 * 7489 = 262115 blocks fit; 35 * 7490 = 262150 do not, although
+    # n_views * nu (59920) is far below the limit
+    for n_views, fits in ((7489, True), (7490, False)):
+        g = _tall_detector_geometry(lib, n_views)
+        assert (35 * n_views <= limit) == fits
+        vol = torch.zeros(g.vol_shape, device="cuda")
+        y = torch.zeros(g.sino_shape, device="cuda")
+        r = torch.empty(g.sino_shape, device="cuda")
+        s = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        if fits:
+            lib.cbct_residual_static(g, vol, y, r, s)
+            assert float(s.item()) == 0.0
+        else:
+            with pytest.raises(lib.CbctError) as err:
+                lib.cbct_residual_static(g, vol, y, r, s)
+            assert err.value.status == 6
+        del vol, y, r
