@@ -345,6 +345,8 @@ extern "C" cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, cbct
         v.cols = L.d_cols;
         v.bp_cap = 0;
         v.bs_cap = 0;
+        v.bp_zc = 0;
+        v.bp_zc = bp_choose_zc(v, det, d.angles);
         v.bp_cap = bp_patch_floats(v, det, d.angles);
         v.bs_cap = bs_patch_floats(v, det, d.angles);
         L.drho = drho;

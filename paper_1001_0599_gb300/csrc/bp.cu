@@ -514,7 +514,7 @@ bp_kernel(VolGeom g, DetGeom d, const void *__restrict__ sino, int st, const flo
 }
 
 #if BP_MODE_UNIT == 0
-static int bp_zc(const VolGeom &v) { return v.nz <= 32 ? 1 : 2; }
+static int bp_zc(const VolGeom &v) { return v.bp_zc > 0 ? v.bp_zc : (v.nz <= 32 ? 1 : 2); }
 
 static int bp_zblocks(const VolGeom &v) { return (v.nz + 32 * bp_zc(v) - 1) / (32 * bp_zc(v)); }
 
@@ -581,6 +581,17 @@ int bp_patch_floats(const VolGeom &v, const DetGeom &d, const double *angles)
 {
     const long cap_max = 48L * 1024L;   // floats: 192 KB
     return (int)std::min<long>(bp_patch_floats_tile(v, d, angles, 32 * bp_zc(v), bp_nr_variant(v, d)), cap_max);
+}
+
+// z chunks per lane: two (64 z voxels per block) unless the grid is 32 deep
+// or less, or the taller patch of 64 z voxels would not fit shared memory for
+// every tile and view (the blocks that do not fit read rows from global
+// memory at a fraction of the speed and run far longer than the rest).
+int bp_choose_zc(const VolGeom &v, const DetGeom &d, const double *angles)
+{
+    if (v.nz <= 32) return 1;
+    const long cap_max = 48L * 1024L;
+    return bp_patch_floats_tile(v, d, angles, 64, bp_nr_variant(v, d)) <= cap_max ? 2 : 1;
 }
 
 // The same for tiles of BP_TX x BP_TY columns and tz z values with nr zero

@@ -40,6 +40,7 @@ struct VolGeom {
     const RayCol *cols;        // [n_views][nu]
     int bp_cap;                // largest staged detector patch of the transpose, floats (0: bound)
     int bs_cap;                // staged patch of the stream-K transpose (bps.cu), floats (0: not used)
+    int bp_zc;                 // z chunks per lane of bp.cu's transpose (0: by nz alone)
 };
 
 struct DetGeom {
@@ -259,6 +260,7 @@ int bp_view_groups(const VolGeom &v, const DetGeom &d);
 size_t bp_split_floats(const VolGeom &v, const DetGeom &d);
 size_t bp_smem_bytes(const VolGeom &v, const DetGeom &d);
 int bp_patch_floats(const VolGeom &v, const DetGeom &d, const double *angles);
+int bp_choose_zc(const VolGeom &v, const DetGeom &d, const double *angles);
 int bp_patch_floats_tile(const VolGeom &v, const DetGeom &d, const double *angles, int tz, int nr);
 int bp_rows_needed(const VolGeom &v, const DetGeom &d);   // most detector rows one voxel's z tent spans
 size_t bp_smem_bound(const VolGeom &v, const DetGeom &d);
