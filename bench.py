@@ -523,6 +523,8 @@ def main():
     # roofline of the dominant kernel
     roof = roofline(prof, prof_levels, wl)
     bandwidth = projector_bandwidth(prof_levels, wl)
+    if bandwidth is not None:
+        add_gather_peak(bandwidth, wl)
     peaks = measured_peaks()
     workload, metric = workload_description(args)
     line = {"metric": metric, "value": sec_per_scan, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -829,6 +831,47 @@ def projector_bandwidth(prof_levels, wl):
     out["note"] = ("not HBM-bound: the per-call working set sits in L2 and both kernels are bound by "
                    "instruction issue; see roofline")
     return out
+
+
+def gather_peak(wl, repeats: int = 5):
+    """Peak trilinear gather rate on this GPU: the library's gather
+    microbenchmark (cbct_gather_bench: warps walking ray lines, 32 lanes on
+    32 neighbouring detector rows, 8 read-only loads per lane and sample) over
+    an L2-resident volume of the workload's finest grid, timed with CUDA
+    events on the launching stream after 3 warm-up launches; the best of
+    ``repeats`` launches."""
+    import torch
+    from paper_1001_0599_gb300 import cbct
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    n_lines, n_samples = sms * 256, 256
+    vol = torch.rand((wl.nx, wl.ny, wl.nz), device="cuda")
+    out = torch.empty(n_lines * 32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        cbct.cbct_gather_bench(vol, n_lines, n_samples, out)
+    best = float("inf")
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cbct.cbct_gather_bench(vol, n_lines, n_samples, out)
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    samples = n_lines * 32 * n_samples
+    return {"samples_per_s": samples / best, "gbs": 32.0 * samples / best / 1e9, "ms": best * 1e3,
+            "volume": [wl.nx, wl.ny, wl.nz],
+            "how": (f"cbct_gather_bench: {n_lines} warps x 32 lanes x {n_samples} trilinear samples (8 read-only "
+                    "loads each) from an L2-resident volume, best of 5 launches by CUDA events")}
+
+
+def add_gather_peak(bandwidth, wl):
+    """Gathered bytes of the projector pair as a fraction of the measured
+    gather peak (the third roofline of the pair, beside HBM and FP32 issue)."""
+    peak = gather_peak(wl)
+    bandwidth["gather_peak"] = peak
+    for name in ("forward_residual", "back_project_step"):
+        if name in bandwidth:
+            bandwidth[name]["frac_of_gather_peak"] = bandwidth[name]["samples_per_s"] / peak["samples_per_s"]
 
 
 def roofline(prof, prof_levels, wl):

@@ -374,6 +374,16 @@ cbct_status cbct_server_query(cbct_server *server, cbct_server_info *info);
 const char *cbct_last_error(void);
 /* Library kernel launches since load (all threads). */
 int64_t cbct_launch_count(void);
+/* Gather microbenchmark for the measurement of the projector pair (no
+ * counterpart in the paper): n_lines warps each walk an in-plane line of
+ * n_samples samples through d_vol (nx*ny*nz floats, z fastest, device,
+ * every size >= 2), their 32 lanes taking 32 neighbouring detector rows, and
+ * every lane gathers one trilinear footprint (8 values, 32 bytes) per
+ * sample with plain read-only loads. Writes one sum per lane to d_out
+ * (n_lines*32 floats, device). Time it on the stream to get the gather rate,
+ * n_lines * 32 * n_samples footprints per launch. */
+cbct_status cbct_gather_bench(const float *d_vol, int nx, int ny, int nz, int n_lines, int n_samples,
+                              float *d_out, void *stream);
 /* Per-kernel timing with CUDA events on the launch stream: while enabled,
  * every launch is bracketed by two events; cbct_profile_collect waits for
  * them and adds their durations to per-kernel totals. Kernel ids

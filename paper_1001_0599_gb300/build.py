@@ -23,7 +23,7 @@ SOURCES = [("api.cu", "api.o", ()), ("fp.cu", "fp.o", ())] + \
     [("bp.cu", f"bp{u}.o", (f"-DBP_MODE_UNIT={u}",)) for u in range(6)] + \
     [("bps.cu", f"bps{u}.o", (f"-DBS_UNIT={u}",)) for u in range(3)] + \
     [("tv.cu", "tv.o", ()), ("misc.cu", "misc.o", ()), ("noalloc.cu", "noalloc.o", ()), ("eq6.cu", "eq6.o", ()),
-                                                                                     ("serve.cu", "serve.o", ())]
+     ("gather.cu", "gather.o", ()), ("serve.cu", "serve.o", ())]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -155,6 +155,8 @@ def load() -> ctypes.CDLL:
     L.cbct_reconstruct_host.argtypes = [_P, _P, _P, ctypes.POINTER(ReconParams), _P, ctypes.c_size_t,
                                         ctypes.POINTER(ReconStats), _P]
     L.cbct_reconstruct_host.restype = st
+    L.cbct_gather_bench.argtypes = [_P] + [ctypes.c_int] * 5 + [_P, _P]
+    L.cbct_gather_bench.restype = st
     L.cbct_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]
     L.cbct_server_create.restype = st
     L.cbct_server_destroy.argtypes = [_P]
@@ -450,6 +452,17 @@ def cbct_reconstruct_host(geom: Geometry, h_sino: np.ndarray, h_vol: np.ndarray,
 
 def cbct_last_error() -> str:
     return load().cbct_last_error().decode()
+
+
+def cbct_gather_bench(vol, n_lines: int, n_samples: int, out, stream=None) -> None:
+    """cbct_gather_bench: the trilinear gather microbenchmark over the CUDA
+    volume ``vol`` (nx, ny, nz); ``out`` holds n_lines * 32 floats."""
+    nx, ny, nz = vol.shape
+    import torch
+    if out.numel() < n_lines * 32:
+        raise ValueError("out must hold n_lines * 32 floats")
+    _check(load().cbct_gather_bench(_dev(vol, "vol", torch.float32), nx, ny, nz, n_lines, n_samples,
+                                    _dev(out, "out", torch.float32), _stream(stream)))
 
 
 def cbct_launch_count() -> int:

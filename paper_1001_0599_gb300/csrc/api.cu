@@ -1039,6 +1039,16 @@ extern "C" const char *cbct_last_error(void) { return g_err.c_str(); }
 
 extern "C" int64_t cbct_launch_count(void) { return g_launches.load(); }
 
+extern "C" cbct_status cbct_gather_bench(const float *d_vol, int nx, int ny, int nz, int n_lines, int n_samples,
+                                         float *d_out, void *stream)
+{
+    if (!d_vol || !d_out) return fail(CBCT_ERR_INVALID_ARG, "NULL device pointer");
+    if (nx < 2 || ny < 2 || nz < 2 || n_lines < 1 || n_samples < 1)
+        return fail(CBCT_ERR_INVALID_ARG, "volume must be at least 2 voxels along each axis, lines and samples >= 1");
+    CUDA_TRY(launch_gather(d_vol, nx, ny, nz, n_lines, n_samples, d_out, (cudaStream_t)stream));
+    return ok();
+}
+
 extern "C" cbct_status cbct_profile_enable(int on)
 {
     g_prof_on = on != 0;

@@ -287,6 +287,10 @@ cudaError_t launch_bs(const VolGeom &v, const DetGeom &d, const void *sino, int 
 
 // Eq. 6 voxel-driven gradient (eq6.cu). mode 0: out = G(T); mode 1:
 // out = f - scale G(T) with scale = scale_val (* *d_scale when given)
+// trilinear gather microbenchmark (gather.cu)
+cudaError_t launch_gather(const float *vol, int nx, int ny, int nz, int n_lines, int n_samples, float *out,
+                          cudaStream_t s);
+
 cudaError_t launch_eq6(const VolGeom &v, const DetGeom &d, const Eq6Geom &e, const float *T, const float *f,
                        float *out, const double *d_scale, double scale_val, int mode, cudaStream_t s);
 
