@@ -449,7 +449,7 @@ static Layout layout(const cbct_geometry *G, const cbct_recon_params *p, bool ho
     off = align_up(off + sizeof(DevState));
     int np = fp_grid_blocks(G->det);
     for (int l = 0; l < G->n_levels; l++) np = std::max(np, bp_grid_blocks(G->lev[l].vg));
-    np = std::max(np, 4 * rof_grid_blocks());
+    np = std::max(np, 4 * rof_bricks(v0.nx, v0.ny, v0.nz));
     L.n_partials = np;
     L.partials = off;
     off = align_up(off + sizeof(double) * (size_t)np);

@@ -336,6 +336,8 @@ struct RofArgs {
                           // every bounded wait expires and the kernel reports a timeout
 };
 int rof_grid_blocks();
+int rof_bricks(int nx, int ny, int nz);    // partial sums of a solve: 4 per brick
+void set_rof_grid_share(int k);            // this thread's solves use 1/k of the GPU
 cudaError_t launch_rof(const RofArgs &a, cudaStream_t s);
 
 // Read-only views of a geometry handle and error reporting (api.cu), for

@@ -59,6 +59,10 @@ CASES = {
     # a single voxel
     "single_voxel": synthetic.Workload("single_voxel", 1, 1, 1, 2.0, 2.0, 2.0, 9, 7, 1.0, 1.0, 3,
                                        sad=100.0, sdd=150.0),
+    # ragged bricks along y and z on a grid the ROF kernel stages with tensor copies
+    # (z a multiple of 4 and at least the 40-slice staging box)
+    "ragged_tma": synthetic.Workload("ragged_tma", 40, 36, 44, 1.0, 1.0, 1.0, 64, 48, 1.2, 1.2, 6, sad=300.0,
+                                     sdd=450.0),
     # more than 1024 detector rows: exercises the warp-per-column projector variant
     "very_tall": synthetic.Workload("very_tall", 10, 9, 300, 2.0, 2.0, 0.3, 9, 1100, 2.5, 0.35, 2,
                                     sad=300.0, sdd=450.0),

@@ -25,7 +25,7 @@ def _pair(og, seed, scale=0.02):
     return f, g
 
 
-@pytest.mark.parametrize("case", ["small", "odd", "one_slice", "tall"])
+@pytest.mark.parametrize("case", ["small", "odd", "one_slice", "tall", "ragged_tma"])
 def test_energy_and_gradient(lib, orc, case):
     import torch
     wl, geom, og = geometries(case)
@@ -42,7 +42,7 @@ def test_energy_and_gradient(lib, orc, case):
     assert d2 == pytest.approx(float(np.mean(dref * dref)), rel=1e-5)
 
 
-@pytest.mark.parametrize("case", ["small", "odd"])
+@pytest.mark.parametrize("case", ["small", "odd", "ragged_tma"])
 def test_trial_energy(lib, orc, case):
     import torch
     wl, geom, og = geometries(case)
@@ -57,7 +57,7 @@ def test_trial_energy(lib, orc, case):
     assert float(out.item()) == pytest.approx(orc.rof_energy(og, ftrial, g, lam, tau, eps), rel=1e-6)
 
 
-@pytest.mark.parametrize("case", ["small", "odd"])
+@pytest.mark.parametrize("case", ["small", "odd", "ragged_tma"])
 def test_rof_solve_matches_oracle(lib, orc, case):
     import torch
     wl, geom, og = geometries(case)
