@@ -80,6 +80,8 @@ def parse():
                          "mixed scans through the serving runtime (latency percentiles, throughput)")
     ap.add_argument("--serve-scans", type=int, default=None,
                     help="scans in the serving stream (serve mode: 64; the default line's serve block: 32)")
+    ap.add_argument("--serve-concurrency", type=int, default=4,
+                    help="reconstructions the server runs at once (compute streams)")
     ap.add_argument("--serve-loads", default=None,
                     help="arrival rates as fractions of the sequential capacity (serve mode: 0.5,0.8,1.0; "
                          "the default line's serve block: 0.8,1.0)")
@@ -551,7 +553,8 @@ def main():
         del ws, d_y, vol, flush
         torch.cuda.empty_cache()
         line["serve"] = serve_summary(serve_measure(args.serve_scans or 32,
-                                                    parse_loads(args.serve_loads or "0.8,1.0"), "f32", local))
+                                                    parse_loads(args.serve_loads or "0.8,1.0"), "f32", local,
+                                                    args.serve_concurrency))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -595,7 +598,7 @@ def serve_bench(args, rank, world, local):
     table of serve_measure on --serve-scans scans (default 64) at loads
     0.5, 0.8 and 1.0 of the sequential capacity."""
     res = serve_measure(args.serve_scans or 64, parse_loads(args.serve_loads or "0.5,0.8,1.0"), args.storage,
-                        local)
+                        local, args.serve_concurrency)
     if rank == 0:
         print(json.dumps(res), flush=True)
     return 0
@@ -609,11 +612,24 @@ def serve_summary(res):
             "scans": res["scans"], "loads": [{"load": r["load"], **{k: r[k] for k in keep}} for r in res["loads"]],
             "sequential_scans_per_min": res["sequential"]["scans_per_min"],
             "server_burst_scans_per_min": res["server_burst"]["scans_per_min"],
-            "bit_identical_to_sequential": res["bit_identical_to_sequential"],
+            "bit_identical_to_sequential": res["bit_identical_to_sequential"], "concurrency": res["concurrency"],
             "workload": res["config"]["workload"], "clocks": res["clocks"]}
 
 
-def serve_measure(n_scans, loads, storage, local):
+def warm_up_server(srv, scans, geoms, sparams, lanes):
+    """Submit `lanes` scans of every shape at once and wait for them, so the
+    slots that scans of a shape occupy side by side exist and hold their
+    captured graphs before anything is timed."""
+    import torch
+    first = {key: next(s for s in scans if s[0] == key) for key in geoms}
+    for key, (wl, g) in geoms.items():
+        tickets = [srv.submit(g, sparams, first[key][2], torch.empty(g.vol_shape, dtype=torch.float32).pin_memory())
+                   for _ in range(lanes)]
+        for t in tickets:
+            srv.wait(t)
+
+
+def serve_measure(n_scans, loads, storage, local, lanes=4):
     """A stream of n_scans scans drawn from 4 grids x 2 detectors x 4 view
     counts, each reconstructed with 50 FBS-TV iterations (3-level multigrid
     20/15/15), arriving as a Poisson stream at the given fractions of the
@@ -690,14 +706,11 @@ def serve_measure(n_scans, loads, storage, local):
     except Exception:
         pass
     sampler = ClockSampler(uuid)
-    srv = cbct.Server(use_graphs=True)
+    srv = cbct.Server(use_graphs=True, concurrency=lanes)
     outs = [torch.empty(g.vol_shape, dtype=torch.float32).pin_memory() for _, g, _, _ in scans]
-    # warm-up: one scan per shape captures its slot's graph
-    warm = [srv.submit(g, sparams, scans[[s[0] for s in scans].index(key)][2],
-                       outs[0].new_empty(g.vol_shape).pin_memory())
-            for key, (wl, g) in geoms.items()]
-    for t in warm:
-        srv.wait(t)
+    # warm-up: `lanes` scans per shape at once capture the graphs of the slots
+    # that scans of that shape occupy side by side
+    warm_up_server(srv, scans, geoms, sparams, lanes)
     identical = True
     sampler.start()
     for load in loads:
@@ -728,10 +741,8 @@ def serve_measure(n_scans, loads, storage, local):
     info = srv.query()
     srv.close()
     # back-to-back stream (all scans submitted at once): the throughput ceiling
-    srv = cbct.Server(use_graphs=True)
-    for t in [srv.submit(g, sparams, scans[[s[0] for s in scans].index(key)][2],
-                         outs[0].new_empty(g.vol_shape).pin_memory()) for key, (wl, g) in geoms.items()]:
-        srv.wait(t)
+    srv = cbct.Server(use_graphs=True, concurrency=lanes)
+    warm_up_server(srv, scans, geoms, sparams, lanes)
     t0 = time.perf_counter()
     tickets = [srv.submit(g, sparams, y, o) for (key, g, y, gi), o in zip(scans, outs)]
     res = [srv.wait(t) for t in tickets]
@@ -750,7 +761,7 @@ def serve_measure(n_scans, loads, storage, local):
             "sequential": {"scans_per_min": 60.0 * capacity, "total_s": seq_total,
                            "mean_service_s": float(np.mean(service))},
             "server_burst": {"scans_per_min": 60.0 * len(scans) / burst, "total_s": burst},
-            "loads": results, "storage": storage, "scans": len(scans),
+            "loads": results, "storage": storage, "scans": len(scans), "concurrency": lanes,
             "bit_identical_to_sequential": bool(identical) if storage == "f32" else None,
             "rms_error_vs_phantom": {"sequential_f32": float(np.mean(rms)), "server": float(np.mean(rms_srv)),
                                      "max_rel_diff_per_scan": float(max(abs(a - b) / b for a, b in

@@ -317,10 +317,14 @@ cbct_status cbct_reconstruct_host(const cbct_geometry *geom, const float *h_sino
  * is admitted, in arrival order, when its slot fits in the arena (an idle
  * slot of the same geometry and parameters is reused; idle slots of other
  * shapes are evicted, least recently used first, to make room). Admitted
- * scans are copied in on a host-to-device stream, reconstructed one at a time
- * on a compute stream (the TV step is a grid-wide cooperative kernel that
- * fills the GPU, so reconstructions are serialised), and copied out on a
- * device-to-host stream, so copies overlap computation. With use_graphs, the
+ * scans are copied in on a host-to-device stream, reconstructed on one of
+ * `concurrency` compute streams (the one with the least work queued), and
+ * copied out on that stream's device-to-host stream, so copies overlap
+ * computation and small scans share the GPU. The TV step is a grid-wide
+ * cooperative kernel; with concurrency k each solve's grid takes 1/k of the
+ * GPU's resident capacity, so k solves fit at once, and its sums do not
+ * depend on the grid size, so a served scan equals the same scan
+ * reconstructed directly, bit for bit. With use_graphs, the
  * first reconstruction in a slot is captured as a CUDA graph and every later
  * scan in that slot replays it (one launch per scan).
  *
@@ -336,6 +340,8 @@ typedef struct {
     size_t arena_bytes;   /* device bytes for resident scans; 0: half the free memory, at most 64 GiB */
     int max_resident;     /* resident slots at most (0: no limit) */
     int use_graphs;       /* 1: capture each slot's reconstruction once and replay it */
+    int concurrency;      /* reconstructions in flight at once, each on its own compute stream
+                             with its TV solves on 1/concurrency of the GPU (0 or 1: one at a time) */
 } cbct_server_config;
 
 typedef struct {

@@ -80,7 +80,8 @@ class ReconStats(ctypes.Structure):
 
 
 class ServerConfig(ctypes.Structure):
-    _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_resident", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_resident", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("concurrency", ctypes.c_int)]
 
 
 class ScanResult(ctypes.Structure):
@@ -520,9 +521,10 @@ class Server:
     into resident slots of one device arena and reconstructs them in arrival
     order, overlapping copies with computation (see include/cbct.h)."""
 
-    def __init__(self, arena_bytes: int = 0, max_resident: int = 0, use_graphs: bool = True):
+    def __init__(self, arena_bytes: int = 0, max_resident: int = 0, use_graphs: bool = True,
+                 concurrency: int = 1):
         L = load()
-        self.cfg = ServerConfig(int(arena_bytes), int(max_resident), 1 if use_graphs else 0)
+        self.cfg = ServerConfig(int(arena_bytes), int(max_resident), 1 if use_graphs else 0, int(concurrency))
         h = _P()
         _check(L.cbct_server_create(ctypes.byref(self.cfg), ctypes.byref(h)))
         self.handle = h.value

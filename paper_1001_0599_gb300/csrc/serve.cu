@@ -7,15 +7,22 @@
 //   scheduler  -- admits queued scans in arrival order (reusing an idle slot of
 //                 the same geometry and parameters, else allocating one, else
 //                 evicting idle slots least recently used first, else waiting
-//                 for a completion), then enqueues: host-to-device copy on the
-//                 copy-in stream, the reconstruction on the compute stream
-//                 (after an event on the copy), device-to-host copies on the
-//                 copy-out stream (after an event on the compute);
-//   completion -- waits on each scan's final event in issue order, stamps the
-//                 times, frees the slot for reuse and wakes the waiters.
-// Reconstructions are serialised on one compute stream: the TV step runs as a
-// cooperative kernel sized to fill every SM, and two such grids are not
-// guaranteed to be co-resident. With graphs enabled, a slot's first
+//                 for a completion), picks the compute lane with the least
+//                 work queued, then enqueues: host-to-device copy on the
+//                 copy-in stream, the reconstruction on the lane's compute
+//                 stream (after an event on the copy), device-to-host copies
+//                 on the lane's copy-out stream (after an event on the
+//                 compute);
+//   completion -- waits for each scan's final event (in issue order with one
+//                 lane; by polling with several), stamps the times, frees the
+//                 slot for reuse and wakes the waiters.
+// With k lanes, k reconstructions run at once. The TV step is a cooperative
+// kernel whose blocks wait on one another; the scheduler thread launches it
+// on 1/k of the GPU's resident capacity, so the k solves in flight always
+// fit together, and the other kernels never wait on anything, so a solve
+// whose blocks are not yet resident gets them as those kernels drain. The
+// solve's sums are independent of its grid size, so a served scan equals a
+// direct reconstruction bit for bit. With graphs enabled, a slot's first
 // reconstruction is captured (on a private stream) and instantiated; later
 // scans in the slot replay the graph with a single launch.
 #include "cbct_internal.cuh"
@@ -35,6 +42,8 @@
 namespace cbct {
 void set_thread_quiet(bool quiet);
 }
+
+constexpr int kMaxLanes = 16;
 
 using namespace cbct;
 
@@ -116,6 +125,8 @@ struct Job {
     cbct_recon_stats *h_stats = nullptr;
     cbct_scan_result res{};
     int slot = -1;
+    int lane = 0;
+    double cost = 0.0;   // work estimate: rays x in-plane voxels along a ray
     cudaEvent_t ev_in = nullptr, ev_start = nullptr, ev_stop = nullptr, ev_out = nullptr;
     bool done = false;
 };
@@ -144,7 +155,10 @@ struct cbct_server {
     cbct_server_config cfg{};
     char *base = nullptr;
     std::unique_ptr<Arena> arena;
-    cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr, s_cap = nullptr;
+    cudaStream_t s_in = nullptr, s_cap = nullptr;
+    int lanes = 1;
+    cudaStream_t s_comp[kMaxLanes] = {}, s_out[kMaxLanes] = {};
+    double lane_work[kMaxLanes] = {};   // cost of the scans in flight per lane
     std::chrono::steady_clock::time_point t0;
 
     std::mutex mu;
@@ -285,6 +299,8 @@ void scheduler_loop(cbct_server *S)
 {
     cudaSetDevice(S->device);
     set_thread_quiet(true);
+    // the TV solves this thread launches (directly or into graphs) take 1/lanes of the GPU
+    set_rof_grid_share(S->lanes);
     std::unique_lock<std::mutex> lk(S->mu);
     while (true) {
         S->cv_sched.wait(lk, [&] { return S->stop || !S->queue.empty(); });
@@ -305,13 +321,25 @@ void scheduler_loop(cbct_server *S)
         j->slot = si;
         j->res.slot = si;
         j->res.t_admit = S->now();
+        // the lane with the least work in flight
+        int lane = 0;
+        for (int l = 1; l < S->lanes; l++)
+            if (S->lane_work[l] < S->lane_work[lane]) lane = l;
+        j->lane = lane;
+        {
+            const VolGeom *v = geometry_level(j->geom, 0);
+            const DetGeom *d = geometry_detector(j->geom);
+            j->cost = (double)d->n_views * d->nv * d->nu * (double)std::max(v->nx, v->ny);
+        }
+        S->lane_work[lane] += j->cost;
+        cudaStream_t s_comp = S->s_comp[lane], s_out = S->s_out[lane];
         // issue (the lock is held: slots and the arena are not touched elsewhere
         // while this runs, and the enqueue calls do not block)
         cbct_status st = CBCT_OK;
         bool ok = cudaMemcpyAsync(sl.sino, j->h_sino, sizeof(float) * sl.nray, cudaMemcpyHostToDevice,
                                   S->s_in) == cudaSuccess &&
                   cudaEventRecord(j->ev_in, S->s_in) == cudaSuccess &&
-                  cudaStreamWaitEvent(S->s_comp, j->ev_in, 0) == cudaSuccess;
+                  cudaStreamWaitEvent(s_comp, j->ev_in, 0) == cudaSuccess;
         if (ok && S->cfg.use_graphs && !sl.graph && !sl.graph_failed) {
             if (capture_slot(S, sl)) {
                 S->graphs_captured++;
@@ -320,29 +348,30 @@ void scheduler_loop(cbct_server *S)
                 S->graph_failures++;
             }
         }
-        ok = ok && cudaEventRecord(j->ev_start, S->s_comp) == cudaSuccess;
+        ok = ok && cudaEventRecord(j->ev_start, s_comp) == cudaSuccess;
         if (ok) {
             if (sl.graph) {
-                ok = cudaGraphLaunch(sl.graph, S->s_comp) == cudaSuccess;
+                ok = cudaGraphLaunch(sl.graph, s_comp) == cudaSuccess;
                 j->res.graph_replay = 1;
             } else {
-                st = enqueue_recon(sl, S->s_comp);
+                st = enqueue_recon(sl, s_comp);
                 ok = st == CBCT_OK;
             }
         }
-        ok = ok && cudaEventRecord(j->ev_stop, S->s_comp) == cudaSuccess &&
-             cudaStreamWaitEvent(S->s_out, j->ev_stop, 0) == cudaSuccess &&
-             cudaMemcpyAsync(j->h_vol, sl.vol, sizeof(float) * sl.nvox, cudaMemcpyDeviceToHost, S->s_out) ==
+        ok = ok && cudaEventRecord(j->ev_stop, s_comp) == cudaSuccess &&
+             cudaStreamWaitEvent(s_out, j->ev_stop, 0) == cudaSuccess &&
+             cudaMemcpyAsync(j->h_vol, sl.vol, sizeof(float) * sl.nvox, cudaMemcpyDeviceToHost, s_out) ==
                  cudaSuccess &&
              (!j->h_stats || cudaMemcpyAsync(j->h_stats, sl.stats, sizeof(cbct_recon_stats),
-                                             cudaMemcpyDeviceToHost, S->s_out) == cudaSuccess) &&
-             cudaEventRecord(j->ev_out, S->s_out) == cudaSuccess;
+                                             cudaMemcpyDeviceToHost, s_out) == cudaSuccess) &&
+             cudaEventRecord(j->ev_out, s_out) == cudaSuccess;
         if (!ok) {
             // work may be partially enqueued: let it drain before the slot is reused
             cudaGetLastError();
             cudaStreamSynchronize(S->s_in);
-            cudaStreamSynchronize(S->s_comp);
-            cudaStreamSynchronize(S->s_out);
+            cudaStreamSynchronize(s_comp);
+            cudaStreamSynchronize(s_out);
+            S->lane_work[lane] -= j->cost;
             sl.busy = false;
             fail_job(S, j, st != CBCT_OK ? st : CBCT_ERR_CUDA);
             S->cv_done.notify_all();
@@ -351,6 +380,22 @@ void scheduler_loop(cbct_server *S)
         S->inflight.push_back(j);
         S->cv_done.notify_all();
     }
+}
+
+void complete_job(cbct_server *S, const std::shared_ptr<Job> &j, cudaError_t e)
+{
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, j->ev_start, j->ev_stop);
+    Slot &sl = S->slots[j->slot];
+    j->res.gpu_ms = ms;
+    j->res.status = e == cudaSuccess ? CBCT_OK : CBCT_ERR_CUDA;
+    if (e == cudaSuccess && j->h_stats) j->res.recon_flags = j->h_stats->flags;
+    j->res.t_done = S->now();
+    j->done = true;
+    S->lane_work[j->lane] -= j->cost;
+    sl.busy = false;
+    sl.last_used = ++S->use_clock;
+    S->completed++;
 }
 
 void completion_loop(cbct_server *S)
@@ -364,22 +409,35 @@ void completion_loop(cbct_server *S)
             if (S->stop && S->queue.empty()) break;
             continue;
         }
-        std::shared_ptr<Job> j = S->inflight.front();
-        lk.unlock();
-        const cudaError_t e = cudaEventSynchronize(j->ev_out);
-        float ms = 0.f;
-        if (e == cudaSuccess) cudaEventElapsedTime(&ms, j->ev_start, j->ev_stop);
-        lk.lock();
-        S->inflight.pop_front();
-        Slot &sl = S->slots[j->slot];
-        j->res.gpu_ms = ms;
-        j->res.status = e == cudaSuccess ? CBCT_OK : CBCT_ERR_CUDA;
-        if (e == cudaSuccess && j->h_stats) j->res.recon_flags = j->h_stats->flags;
-        j->res.t_done = S->now();
-        j->done = true;
-        sl.busy = false;
-        sl.last_used = ++S->use_clock;
-        S->completed++;
+        if (S->lanes == 1) {
+            // one lane completes in issue order: wait for the oldest scan
+            std::shared_ptr<Job> j = S->inflight.front();
+            lk.unlock();
+            const cudaError_t e = cudaEventSynchronize(j->ev_out);
+            lk.lock();
+            S->inflight.pop_front();
+            complete_job(S, j, e);
+        } else {
+            // several lanes finish out of order: collect every finished scan, else
+            // poll again shortly
+            bool any = false;
+            for (auto it = S->inflight.begin(); it != S->inflight.end();) {
+                const cudaError_t e = cudaEventQuery((*it)->ev_out);
+                if (e == cudaErrorNotReady) {
+                    ++it;
+                    continue;
+                }
+                complete_job(S, *it, e);
+                it = S->inflight.erase(it);
+                any = true;
+            }
+            if (!any) {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(100));
+                lk.lock();
+                continue;
+            }
+        }
         S->cv_done.notify_all();
         S->cv_sched.notify_all();
     }
@@ -394,6 +452,8 @@ extern "C" cbct_status cbct_server_create(const cbct_server_config *cfg, cbct_se
     cbct_server_config c{};
     if (cfg) c = *cfg;
     if (c.max_resident < 0) return report_error(CBCT_ERR_INVALID_ARG, "max_resident must be >= 0");
+    if (c.concurrency < 0 || c.concurrency > kMaxLanes)
+        return report_error(CBCT_ERR_INVALID_ARG, "concurrency must be between 0 and 16");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return report_error(CBCT_ERR_CUDA, "no CUDA device");
     if (c.arena_bytes == 0) {
@@ -411,7 +471,12 @@ extern "C" cbct_status cbct_server_create(const cbct_server_config *cfg, cbct_se
         return report_error(CBCT_ERR_OUT_OF_MEMORY, "cudaMalloc of the serving arena failed");
     }
     S->arena = std::make_unique<Arena>(c.arena_bytes);
-    cudaStream_t *streams[4] = {&S->s_in, &S->s_comp, &S->s_out, &S->s_cap};
+    S->lanes = c.concurrency > 1 ? c.concurrency : 1;
+    std::vector<cudaStream_t *> streams = {&S->s_in, &S->s_cap};
+    for (int l = 0; l < S->lanes; l++) {
+        streams.push_back(&S->s_comp[l]);
+        streams.push_back(&S->s_out[l]);
+    }
     for (cudaStream_t *s : streams)
         if (cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) != cudaSuccess) {
             for (cudaStream_t *t : streams)
@@ -450,9 +515,13 @@ extern "C" void cbct_server_destroy(cbct_server *S)
     }
     for (Slot &sl : S->slots)
         if (sl.graph) cudaGraphExecDestroy(sl.graph);
-    cudaStream_t streams[4] = {S->s_in, S->s_comp, S->s_out, S->s_cap};
+    cudaStream_t streams[2] = {S->s_in, S->s_cap};
     for (cudaStream_t s : streams)
         if (s) cudaStreamDestroy(s);
+    for (int l = 0; l < S->lanes; l++) {
+        if (S->s_comp[l]) cudaStreamDestroy(S->s_comp[l]);
+        if (S->s_out[l]) cudaStreamDestroy(S->s_out[l]);
+    }
     cudaFree(S->base);
     delete S;
 }

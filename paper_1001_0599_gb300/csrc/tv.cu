@@ -401,43 +401,60 @@ __device__ bool sweep(const RofArgs &a, const RofMaps *mp, TvShared &sh, float *
         float part[K];
 #pragma unroll
         for (int q = 0; q < K; q++) part[q] = 0.f;
+        // warp w owns the voxel column lx = w of the brick, lane the slice
+        // z0 + lane, and steps through ly = 0..7
+        const int lx = warp, gx = x0 + lx, gz = z0 + lane;
+        const int hx = lx + 1, hz = lane + SZ0;
+        if (gx < a.nx) {   // warp-uniform
+            float qy_prev = 0.f;   // q_y of the voxel below in y (KIND 0)
 #pragma unroll 2
-        for (int i = 0; i < PER_THREAD; i++) {
-            const int p = warp + i * TV_WARPS;
-            const int lx = p % BX, ly = p / BX;
-            const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lane;
-            if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
-            const int hx = lx + 1, hy = ly + 1, hz = lane + SZ0;
-            float Dx, Dy, Dz;
-            fdiff(a, F, hx, hy, hz, gx, gy, gz, Dx, Dy, Dz);
-            // phi = sqrt(eps^2 + |D f|^2) and 1/phi from one reciprocal square root
-            const float s2 = eps2 + Dx * Dx + Dy * Dy + Dz * Dz;
-            const float inv_phi = rsqrtf(s2);
-            const float phi = s2 * inv_phi;
-            const float diff = F[sidx(hx, hy, hz)] - gv[i];
-            if (KIND == 0) {
-                float div = -(Dx * inv_phi) * a.inv_dx - (Dy * inv_phi) * a.inv_dy - (Dz * inv_phi) * a.inv_dz;
-                if (gx > 0) {
-                    float ex, ey, ez;
-                    fdiff(a, F, hx - 1, hy, hz, gx - 1, gy, gz, ex, ey, ez);
-                    div += ex * rsqrtf(eps2 + ex * ex + ey * ey + ez * ez) * a.inv_dx;
+            for (int i = 0; i < PER_THREAD; i++) {
+                const int ly = i, gy = y0 + ly, hy = ly + 1;
+                if (gy >= a.ny) break;   // warp-uniform
+                float Dx, Dy, Dz;
+                fdiff(a, F, hx, hy, hz, gx, gy, gz, Dx, Dy, Dz);
+                // phi = sqrt(eps^2 + |D f|^2) and 1/phi from one reciprocal square root
+                const float s2 = eps2 + Dx * Dx + Dy * Dy + Dz * Dz;
+                const float inv_phi = rsqrtf(s2);
+                const float phi = s2 * inv_phi;
+                const float diff = F[sidx(hx, hy, hz)] - gv[i];
+                const bool live = gz < a.nz;
+                if (KIND == 0) {
+                    // q = D f / phi here; the backward divergence needs q_x, q_y, q_z of
+                    // the neighbours below: q_z from the lane below (lane 0 evaluates
+                    // its own), q_y from this thread's previous step, q_x evaluated
+                    const float qx = Dx * inv_phi, qy = Dy * inv_phi, qz = Dz * inv_phi;
+                    float div = -qx * a.inv_dx - qy * a.inv_dy - qz * a.inv_dz;
+                    float qz_below = __shfl_up_sync(0xffffffffu, qz, 1);
+                    if (lane == 0 && gz > 0) {
+                        float ex, ey, ez;
+                        fdiff(a, F, hx, hy, hz - 1, gx, gy, gz - 1, ex, ey, ez);
+                        qz_below = ez * rsqrtf(eps2 + ex * ex + ey * ey + ez * ez);
+                    }
+                    if (gz > 0) div += qz_below * a.inv_dz;
+                    if (gy > 0) {
+                        if (i == 0) {
+                            float ex, ey, ez;
+                            fdiff(a, F, hx, hy - 1, hz, gx, gy - 1, gz, ex, ey, ez);
+                            qy_prev = ey * rsqrtf(eps2 + ex * ex + ey * ey + ez * ez);
+                        }
+                        div += qy_prev * a.inv_dy;
+                    }
+                    if (gx > 0) {
+                        float ex, ey, ez;
+                        fdiff(a, F, hx - 1, hy, hz, gx - 1, gy, gz, ex, ey, ez);
+                        div += ex * rsqrtf(eps2 + ex * ex + ey * ey + ez * ez) * a.inv_dx;
+                    }
+                    qy_prev = qy;
+                    if (live) {
+                        const float dj = lam * div + diff * inv_tau;
+                        dout[((size_t)gx * a.ny + gy) * a.nz + gz] = dj;
+                        part[0] += lam * phi + diff * diff * inv_2tau;
+                        part[K - 1] += dj * dj;
+                    }
+                } else if (live) {
+                    part[0] += lam * phi + diff * diff * inv_2tau;
                 }
-                if (gy > 0) {
-                    float ex, ey, ez;
-                    fdiff(a, F, hx, hy - 1, hz, gx, gy - 1, gz, ex, ey, ez);
-                    div += ey * rsqrtf(eps2 + ex * ex + ey * ey + ez * ez) * a.inv_dy;
-                }
-                if (gz > 0) {
-                    float ex, ey, ez;
-                    fdiff(a, F, hx, hy, hz - 1, gx, gy, gz - 1, ex, ey, ez);
-                    div += ez * rsqrtf(eps2 + ex * ex + ey * ey + ez * ez) * a.inv_dz;
-                }
-                const float dj = lam * div + diff * inv_tau;
-                dout[((size_t)gx * a.ny + gy) * a.nz + gz] = dj;
-                part[0] += lam * phi + diff * diff * inv_2tau;
-                part[K - 1] += dj * dj;
-            } else {
-                part[0] += lam * phi + diff * diff * inv_2tau;
             }
         }
         brick_warp_sums<K>(part, sh, it & 1);

@@ -186,3 +186,26 @@ def test_concurrent_submitters(lib):
     assert info.completed == len(scans)
     for (v, status), (rv, _) in zip(outs, ref):
         assert status == 0 and np.array_equal(v, rv)
+
+
+@pytest.mark.parametrize("lanes", [2, 3])
+def test_concurrent_lanes_equal_direct_reconstruction(lib, lanes):
+    # several reconstructions in flight on separate compute streams, each TV
+    # solve on 1/lanes of the GPU: the solve's sums do not depend on its grid
+    # size, so every scan still equals its direct reconstruction bit for bit
+    scans = _scans(lib, ["small", "odd", "tall", "ragged_tma"], 2, seed=4)
+    ref = [_direct(lib, g, p, s) for _, g, p, s in scans]
+    for graphs in (True, False):
+        got, res, info = _serve(lib, scans, use_graphs=graphs, concurrency=lanes)
+        assert info.completed == len(scans)
+        for (v, st), (rv, rst), r in zip(got, ref, res):
+            assert r.status == 0
+            assert np.array_equal(v, rv)
+            assert st.n_iters == rst.n_iters and st.flags == rst.flags
+            assert [st.iters[k].e_rof_last for k in range(st.n_iters)] == \
+                [rst.iters[k].e_rof_last for k in range(rst.n_iters)]
+
+
+def test_concurrency_validation(lib):
+    with pytest.raises(lib.CbctError):
+        lib.Server(concurrency=17)
