@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--validate-model", action="store_true",
+                    help="reference arm: time one full oracle reconstruction of the workload and compare it with "
+                         "the sampled per-operation model on that run's own schedule")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--power-fine", type=int, default=4,
                     help="power iterations on each level after the first, warm-started from the "
@@ -63,7 +66,7 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp16"],
                     help="storage type of the sinograms and of the projector's volume copy "
                          "(FP32 arithmetic throughout)")
-    ap.add_argument("--workload", default="cube40", choices=["paper", "lowdose", "cube40"],
+    ap.add_argument("--workload", default="cube40", choices=["paper", "lowdose", "cube40", "small"],
                     help="cube40: 256^3, 40 views (default); paper: 256x256x128, 40 views; "
                          "lowdose: 256^3, 360 views, 1e4 photons")
     ap.add_argument("--schedule", default=None,
@@ -320,6 +323,30 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def validate_model(args, wl):
+    """One full oracle reconstruction, timed, beside the sampled model of the
+    reference arm evaluated on that reconstruction's own schedule (accepted
+    steps and reductions per ROF solve): the model's error on this machine."""
+    from oracle import oracle as orc
+    from paper_1001_0599_gb300 import synthetic
+    _, y = synthetic.make_problem(wl)
+    g = orc.Geometry.from_workload(wl)
+    power_fine = args.power_fine if len(wl.iters) > 1 else 0
+    oracle_sample_warm(wl)
+    t0 = time.perf_counter()
+    res = orc.reconstruct(g, y, wl.lam, wl.iters, orc.TVParams(eps_tv=1e-5), power_iters=20, clamp=True,
+                          power_iters_fine=power_fine)
+    full = time.perf_counter() - t0
+    levels = [{"power": 20 if lev == 0 or power_fine <= 0 else power_fine, "fbs": []} for lev in range(len(wl.iters))]
+    for it in res.iters:
+        levels[it.level]["fbs"].append({"n_inner": int(it.n_inner), "backtracks": int(sum(it.steps))})
+    schedule = {"levels": levels, "source": "the timed full run"}
+    model, _, units = oracle_sample(wl, schedule)
+    print(json.dumps({"workload": wl.name, "oracle_full_s": full, "model_s": model, "model_over_full": model / full,
+                      "cores": cpu_cores(), "units": units}), flush=True)
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -327,6 +354,8 @@ def run_reference(args, rank, world):
     from paper_1001_0599_gb300 import synthetic
     orc.build()
     wl = synthetic.workload(args.workload)
+    if args.validate_model:
+        return validate_model(args, wl)
     if args.schedule:
         with open(args.schedule) as fh:
             schedule = json.load(fh)

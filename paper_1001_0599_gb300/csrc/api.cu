@@ -960,8 +960,9 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
                 const double eq6_factor = G->lev[gl].dx * G->lev[gl].dy * G->lev[gl].dz / (2.0 * G->desc.du * G->desc.dv);
                 CUDA_TRY(launch_eq6(v, G->det, G->lev[gl].eq6, r, f, g, &st->scale, eq6_factor, 1, s));
             } else if (sto != CBCT_STORAGE_F32) {
-                // Step 1 with y, r and the projector's copy of f stored as `sto`
-                CUDA_TRY(launch_convert(f, CBCT_STORAGE_F32, fsto, sto, nvox(v), s));
+                // Step 1 with y, r and the projector's copy of f stored as `sto`; after
+                // the level's first iteration the ROF solve wrote that copy with f
+                if (it == 0) CUDA_TRY(launch_convert(f, CBCT_STORAGE_F32, fsto, sto, nvox(v), s));
                 CUDA_TRY(launch_forward_st(v, G->det, fsto, ysto, r, sto, nullptr, partials, 2, s));
                 CUDA_TRY(launch_e2(partials, fp_partials_count(v, G->det), inv_m, st, s));
                 CUDA_TRY(launch_back_st(v, G->det, r, sto, f, g, &st->scale, 0.0, 0.0, nullptr, 1, 1,
@@ -988,6 +989,10 @@ static cbct_status recon_core(const cbct_geometry *G, const float *d_sino, float
             a.replay = d_replay ? d_replay + replay_off[k] : nullptr;
             a.level = lev;
             a.tau_dev = &st->tau;
+            if (sto != CBCT_STORAGE_F32 && p->gradient_mode != 1) {
+                a.f_store = fsto;
+                a.store_type = sto;
+            }
             CUDA_TRY(launch_rof(a, s));
         }
         prev = f;

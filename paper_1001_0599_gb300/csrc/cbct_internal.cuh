@@ -332,6 +332,8 @@ struct RofArgs {
     const float *dir;     // mode 2: direction
     const float *cur;     // modes 1, 2: iterate
     int level;
+    void *f_store;        // optional: the solve's result also written here in storage type store_type
+    int store_type;       // cbct_storage of f_store
     int withhold_arrival; // failure-detection check: no block ever completes the barrier, so
                           // every bounded wait expires and the kernel reports a timeout
 };

@@ -465,10 +465,23 @@ __device__ bool sweep(const RofArgs &a, const RofMaps *mp, TvShared &sh, float *
     return true;
 }
 
-// f = cur - s*dir (dir may be null: copy), optionally clamped at 0.
+// f = cur - s*dir (dir may be null: copy), optionally clamped at 0; with
+// `store`, the value is also written to a.f_store rounded to a.store_type
+// (the copy the reduced-storage projector gathers from).
 __device__ void sweep_update(const RofArgs &a, const float *cur, const float *dir, float s, float *f,
-                             bool clamp)
+                             bool clamp, bool store = false)
 {
+    if (store) {
+        const size_t n = (size_t)a.nx * a.ny * a.nz;
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+            float c = __ldcg(cur + i);
+            if (dir) c = __fmaf_rn(-s, __ldcg(dir + i), c);
+            if (clamp) c = fmaxf(c, 0.f);
+            __stcg(f + i, c);
+            st_st(a.f_store, i, c, a.store_type);
+        }
+        return;
+    }
     const size_t n = (size_t)a.nx * a.ny * a.nz;
     const size_t n4 = n / 4;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -550,7 +563,7 @@ rof_kernel(const RofArgs args, const __grid_constant__ RofMaps maps)
     const float *cur = a.start_at_g ? a.g : a.f;
     int cur_map = a.start_at_g ? MAP_G : MAP_F;
     bool wrote_f = !a.start_at_g;
-    bool clamped = false;
+    bool clamped = false, stored = false;
     int n_inner = 0, bt_total = 0, flags = 0;
     double e_first = 0.0, e_last = 0.0;
     const double s0 = a.s0 > 0.0 ? a.s0 : a.tau;
@@ -591,7 +604,9 @@ rof_kernel(const RofArgs args, const __grid_constant__ RofMaps maps)
         const double rel = replay ? 1.0 : fabs(Enew - E0) / E0;
         const bool stop = replay ? (it == n_steps - 1) : (rel < a.rel_tol || it == n_steps - 1);
         const bool do_clamp = a.clamp && stop;
-        sweep_update(a, cur, a.d, (float)step, a.f, do_clamp);
+        const bool do_store = a.f_store != nullptr && stop;
+        sweep_update(a, cur, a.d, (float)step, a.f, do_clamp, do_store);
+        stored = do_store;
         cur = a.f;
         cur_map = MAP_F;
         wrote_f = true;
@@ -610,10 +625,11 @@ rof_kernel(const RofArgs args, const __grid_constant__ RofMaps maps)
         }
         if (!grid_sync<0>(a.st, a.partials, nb, sh)) return;
     }
-    if (!wrote_f || (a.clamp && !clamped)) {
+    if (!wrote_f || (a.clamp && !clamped) || (a.f_store && !stored)) {
         // the loop ended without writing the final iterate: f = clamp(cur)
+        // (and its stored copy)
         if (!grid_sync<0>(a.st, a.partials, nb, sh)) return;
-        sweep_update(a, cur, nullptr, 0.f, a.f, a.clamp != 0);
+        sweep_update(a, cur, nullptr, 0.f, a.f, a.clamp != 0, a.f_store != nullptr);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (a.tv_stats) {

@@ -209,3 +209,32 @@ def test_concurrent_lanes_equal_direct_reconstruction(lib, lanes):
 def test_concurrency_validation(lib):
     with pytest.raises(lib.CbctError):
         lib.Server(concurrency=17)
+
+
+def test_served_scan_matches_oracle(lib, orc):
+    # a small scan served with concurrent lanes against the FP64 oracle run
+    # on the served scan's own step decisions (its statistics), at 1e-4
+    import torch
+    from paper_1001_0599_gb300 import synthetic
+    from gpu_util import TOL_RECON, f32, rel_l2
+    wl = synthetic.workload("small")
+    truth, y = synthetic.make_problem(wl)
+    g = lib.geometry_from_workload(wl)
+    p = orc.TVParams(eps_tv=1e-5)
+    tv = lib.TvParams(p.eps_tv, p.c, p.alpha, p.rel_tol, p.max_inner, p.max_backtracks, p.s0)
+    params = lib.make_recon_params(wl.lam, (6,), tv, power_iters=20)
+    h_sino = torch.from_numpy(f32(y).astype(np.float32)).pin_memory()
+    scans = [("small", g, params, h_sino)] * 3
+    got, res, info = _serve(lib, scans, use_graphs=True, concurrency=3)
+    og = orc.Geometry.from_workload(wl)
+    for (v, st), r in zip(got, res):
+        assert r.status == 0
+        flat = list(st.steps[:st.n_steps])
+        sched, k = [], 0
+        for i in range(st.n_iters):
+            n = int(st.iters[i].n_inner)
+            sched.append(flat[k:k + n])
+            k += n
+        ref = orc.reconstruct(og, f32(y), wl.lam, (6,), p, power_iters=20, replay=sched)
+        assert st.tau[0] == pytest.approx(ref.taus[0], rel=1e-5)
+        assert rel_l2(v.astype(np.float64), ref.f) < TOL_RECON
