@@ -150,11 +150,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def oracle_units(wl):
     """Per-operation seconds of the FP64 oracle on every multigrid level of a
-    workload, from a bounded sample: P over one view; P^T over one and two
-    views (a per-call part -- the private per-thread volumes and their
-    fixed-order sum -- plus a per-view part); and the ROF solve's per-call
-    part, its cost per accepted step (gradient, trial, update) and per
-    further trial (one energy evaluation and update)."""
+    workload, from a bounded sample: P over 4 views spread over the first
+    quarter turn (views differ in cost: an oblique view's rays cross more of
+    a square grid), as the mean per view; P^T over 2 and 4 of those views (a
+    per-call part -- the private per-thread volumes and their fixed-order sum
+    -- plus a per-view part); and the ROF solve's per-call part, its cost per
+    accepted step (gradient, trial, update) and per further trial (one
+    energy evaluation and update)."""
     import numpy as np
     from oracle import oracle as orc
     g = orc.Geometry.from_workload(wl)
@@ -162,26 +164,28 @@ def oracle_units(wl):
     rng = np.random.default_rng(0)
     tv = orc.TVParams(eps_tv=1e-5)
     out = []
+    nv = g.n_views
+    spread = sorted({int(round(k * nv / 16.0)) % nv for k in range(4)})
     for lev in range(levels):
         gl = g.coarse(2 ** (levels - 1 - lev)) if lev < levels - 1 else g
 
-        def sub(k):
+        def sub(idx):
             return orc.Geometry(gl.nx, gl.ny, gl.nz, gl.dx, gl.dy, gl.dz, gl.nu, gl.nv, gl.du, gl.dv, gl.sad,
-                                gl.sdd, gl.angles[:k].copy(), gl.step_ratio)
+                                gl.sdd, gl.angles[idx].copy(), gl.step_ratio)
 
         f = rng.random(gl.vol_shape) * 0.02
-        s1, s2 = sub(1), sub(2)
+        s4, s2 = sub(spread), sub(spread[::2])
         t0 = time.perf_counter()
-        p1 = orc.forward_project(s1, f)
-        t_p = time.perf_counter() - t0
+        p4 = orc.forward_project(s4, f)
+        t_p = (time.perf_counter() - t0) / len(spread)
         p2 = orc.forward_project(s2, f)
-        t0 = time.perf_counter()
-        orc.back_project(s1, p1)
-        t_b1 = time.perf_counter() - t0
         t0 = time.perf_counter()
         orc.back_project(s2, p2)
         t_b2 = time.perf_counter() - t0
-        bt_view = max(t_b2 - t_b1, 0.0)
+        t0 = time.perf_counter()
+        orc.back_project(s4, p4)
+        t_b4 = time.perf_counter() - t0
+        bt_view = max(t_b4 - t_b2, 0.0) / (len(spread) - len(spread[::2]))
         gaux = f + 0.001 * rng.standard_normal(gl.vol_shape)
         t0 = time.perf_counter()
         orc.rof_solve(gl, gaux, wl.lam, 1e-5, tv, replay=[0])
@@ -193,7 +197,8 @@ def oracle_units(wl):
         orc.rof_energy(gl, f, gaux, wl.lam, 1e-5, 1e-5)
         t_e = time.perf_counter() - t0
         step = max(t_r2 - t_r1, 0.0)
-        out.append({"level": lev, "views": gl.n_views, "p_view": t_p, "pt_call": max(t_b1 - bt_view, 0.0),
+        out.append({"level": lev, "views": gl.n_views, "p_view": t_p,
+                    "pt_call": max(t_b2 - bt_view * len(spread[::2]), 0.0),
                     "pt_view": bt_view, "rof_call": max(t_r1 - step, 0.0), "rof_step": step, "rof_trial": t_e})
     return out
 
@@ -235,7 +240,8 @@ def oracle_sample(wl, schedule):
     """Seconds per oracle reconstruction: unit costs timed now, multiplied by
     the schedule's operation counts."""
     units = oracle_units(wl)
-    desc = ("per level: P on 1 view, P^T on 1 and 2 views (per-call and per-view parts), ROF per-call, "
+    desc = ("per level: P on 4 views spread over a quarter turn, P^T on 2 and 4 of them (per-call and per-view "
+            "parts), ROF per-call, "
             "per-step and per-trial costs; times the schedule's counts from " + schedule["source"])
     return oracle_model_seconds(units, schedule), desc, units
 

@@ -133,24 +133,41 @@ def kappa(geom: "cbct.Geometry") -> float:
     return 2.0 * nx * ny * nz / (geom.desc.n_views * nv * nu)
 
 
-def unrolled_data_steps(geom: "cbct.Geometry", y, f0, tau: float, n_iter: int, checkpoint: bool = True):
+def unrolled_data_steps(geom: "cbct.Geometry", y, f0, tau: float, n_iter: int, checkpoint: bool = True,
+                        clamp: bool = False, segment: int = 1):
     """n_iter differentiable iterations of the data step of Algorithm A1,
     f <- f - tau kappa P^T (P f - y) (Sec. II.C.1), differentiable in f0 and
-    y. With checkpoint=True only f is kept per iteration and the backward pass
-    recomputes each iteration's P f. (The data step alone is linear, so autograd
-    saves no tensor for it either way; checkpointing pays once a caller adds
-    stages that save activations.)"""
+    y; with clamp=True each step is followed by the nonnegativity projection
+    of Step 3 (f <- max(f, 0)).
+
+    The data step alone is linear, so autograd saves no tensor for it; the
+    clamp saves its output, one volume per iteration. With checkpoint=True the
+    chain is cut into segments of ``segment`` iterations: only each segment's
+    input volume is kept, and the backward pass recomputes the segment's
+    projections and clamps, so a chain of n iterations holds about
+    n / segment volumes instead of n."""
+    import torch
     import torch.utils.checkpoint as ckpt
 
     k = kappa(geom)
 
     def step(f, y):
-        return f - (tau * k) * back_project(geom, forward_project(geom, f) - y)
+        f = f - (tau * k) * back_project(geom, forward_project(geom, f) - y)
+        return torch.clamp(f, min=0.0) if clamp else f
+
+    def run(f, y, n):
+        for _ in range(n):
+            f = step(f, y)
+        return f
 
     f = f0
-    for _ in range(n_iter):
+    seg = max(int(segment), 1)
+    done = 0
+    while done < n_iter:
+        n = min(seg, n_iter - done)
         if checkpoint and (f.requires_grad or y.requires_grad):
-            f = ckpt.checkpoint(step, f, y, use_reentrant=False)
+            f = ckpt.checkpoint(run, f, y, n, use_reentrant=False)
         else:
-            f = step(f, y)
+            f = run(f, y, n)
+        done += n
     return f
