@@ -572,6 +572,7 @@ def main():
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "clocks": clocks, "gpu_launches": int(launches), "roofline": roof,
             "projector_bandwidth": bandwidth,
+            "tv_sweeps": tv_sweep_bandwidth(st, prof_levels, wl) if args.mode == "recon" else None,
             "e2e": e2e,
             "kernels": {k: {"launches": n // prof_steps, "ms_per_step": ms / prof_steps}
                         for k, (n, ms) in prof.items() if n},
@@ -877,6 +878,38 @@ def projector_bandwidth(prof_levels, wl):
     out["note"] = ("not HBM-bound: the per-call working set sits in L2 and both kernels are bound by "
                    "instruction issue; see roofline")
     return out
+
+
+def tv_sweep_bandwidth(st, prof_levels, wl):
+    """The ROF solves against HBM, per multigrid level: algorithmic bytes of
+    a solve from its own step counts (every accepted step: a gradient sweep
+    reading f and g and writing d, 12 B/voxel; its first trial and every
+    reduction, reading f, d and g, 12 B/voxel; the update reading f and d and
+    writing f, 12 B/voxel), over the solves' time measured by CUDA events."""
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    n_levels = len(wl.iters)
+    sweeps = [0.0] * n_levels
+    solves = [0] * n_levels
+    for k in range(int(st.n_iters)):
+        it = st.iters[k]
+        gl = n_levels - 1 - int(it.level)   # geometry level, 0 = finest
+        sweeps[gl] += 3 * int(it.n_inner) + int(it.backtracks)
+        solves[gl] += 1
+    out = {}
+    for gl in range(n_levels):
+        n, ms = prof_levels.get(gl, {}).get("rof_persistent", (0, 0.0))
+        if not n or ms <= 0 or not solves[gl]:
+            continue
+        ms = ms / n * solves[gl]   # one reconstruction's solves on this level
+        f = 2 ** gl
+        nvox = (wl.nx // f) * (wl.ny // f) * (wl.nz // f)
+        algo = 12.0 * nvox * sweeps[gl]
+        out[str(gl)] = {"solves": solves[gl], "sweeps": int(sweeps[gl]), "algorithmic_bytes": algo,
+                        "ms": ms, "algorithmic_gbs": algo / (ms / 1e3) / 1e9,
+                        "frac_of_hbm": algo / (ms / 1e3) / 1e9 / hbm}
+    return {"levels": out, "hbm_peak_gbs": hbm,
+            "work": "12 B per voxel per sweep (gradient, trial, update), sweeps from this run's step counts"}
 
 
 def gather_peak(wl, repeats: int = 5):
