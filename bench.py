@@ -83,6 +83,8 @@ def parse():
                          "mixed scans through the serving runtime (latency percentiles, throughput)")
     ap.add_argument("--serve-scans", type=int, default=None,
                     help="scans in the serving stream (serve mode: 64; the default line's serve block: 32)")
+    ap.add_argument("--no-serve-reuse", action="store_true",
+                    help="serve without reusing each geometry's power-iteration step sizes")
     ap.add_argument("--serve-concurrency", type=int, default=4,
                     help="reconstructions the server runs at once (compute streams)")
     ap.add_argument("--serve-loads", default=None,
@@ -590,7 +592,7 @@ def main():
         torch.cuda.empty_cache()
         line["serve"] = serve_summary(serve_measure(args.serve_scans or 32,
                                                     parse_loads(args.serve_loads or "0.8,1.0"), "f32", local,
-                                                    args.serve_concurrency))
+                                                    args.serve_concurrency, not args.no_serve_reuse))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -634,7 +636,7 @@ def serve_bench(args, rank, world, local):
     table of serve_measure on --serve-scans scans (default 64) at loads
     0.5, 0.8 and 1.0 of the sequential capacity."""
     res = serve_measure(args.serve_scans or 64, parse_loads(args.serve_loads or "0.5,0.8,1.0"), args.storage,
-                        local, args.serve_concurrency)
+                        local, args.serve_concurrency, not args.no_serve_reuse)
     if rank == 0:
         print(json.dumps(res), flush=True)
     return 0
@@ -648,32 +650,39 @@ def serve_summary(res):
             "scans": res["scans"], "loads": [{"load": r["load"], **{k: r[k] for k in keep}} for r in res["loads"]],
             "sequential_scans_per_min": res["sequential"]["scans_per_min"],
             "server_burst_scans_per_min": res["server_burst"]["scans_per_min"],
+            "server_burst_without_step_reuse_scans_per_min": (res["server_burst_without_step_reuse"] or {}).get(
+                "scans_per_min"),
+            "reuse_steps": res["reuse_steps"],
             "bit_identical_to_sequential": res["bit_identical_to_sequential"], "concurrency": res["concurrency"],
             "workload": res["config"]["workload"], "clocks": res["clocks"]}
 
 
-def warm_up_server(srv, scans, geoms, sparams, lanes):
+def warm_up_server(srv, scans, geoms, sparams, lanes, passes=1):
     """Submit `lanes` scans of every shape at once and wait for them, so the
     slots that scans of a shape occupy side by side exist and hold their
-    captured graphs before anything is timed."""
+    captured graphs before anything is timed. With step reuse a second pass
+    captures the graphs that run with the taus the first pass found."""
     import torch
     first = {key: next(s for s in scans if s[0] == key) for key in geoms}
-    for key, (wl, g) in geoms.items():
-        tickets = [srv.submit(g, sparams, first[key][2], torch.empty(g.vol_shape, dtype=torch.float32).pin_memory())
-                   for _ in range(lanes)]
-        for t in tickets:
-            srv.wait(t)
+    for _ in range(passes):
+        for key, (wl, g) in geoms.items():
+            tickets = [srv.submit(g, sparams, first[key][2],
+                                  torch.empty(g.vol_shape, dtype=torch.float32).pin_memory())
+                       for _ in range(lanes)]
+            for t in tickets:
+                srv.wait(t)
 
 
-def serve_measure(n_scans, loads, storage, local, lanes=4):
+def serve_measure(n_scans, loads, storage, local, lanes=4, reuse_steps=True):
     """A stream of n_scans scans drawn from 4 grids x 2 detectors x 4 view
     counts, each reconstructed with 50 FBS-TV iterations (3-level multigrid
     20/15/15), arriving as a Poisson stream at the given fractions of the
     sequential capacity. The sequential system processes one scan at a time
     through cbct_reconstruct_host (copy in, reconstruct, copy out, wait); the
-    server overlaps copies with compute and replays captured graphs. Outputs
-    are checked bit-identical between the two, so the RMS error is equal by
-    construction."""
+    server overlaps copies with compute and replays captured graphs, and (with
+    reuse_steps) runs every shape's scans after its first with the taus that
+    scan's power iterations found. Outputs are checked bit-identical between
+    the two, so the RMS error is equal by construction."""
     import hashlib
 
     import numpy as np
@@ -742,11 +751,12 @@ def serve_measure(n_scans, loads, storage, local, lanes=4):
     except Exception:
         pass
     sampler = ClockSampler(uuid)
-    srv = cbct.Server(use_graphs=True, concurrency=lanes)
+    passes = 2 if reuse_steps else 1
+    srv = cbct.Server(use_graphs=True, concurrency=lanes, reuse_steps=reuse_steps)
     outs = [torch.empty(g.vol_shape, dtype=torch.float32).pin_memory() for _, g, _, _ in scans]
     # warm-up: `lanes` scans per shape at once capture the graphs of the slots
     # that scans of that shape occupy side by side
-    warm_up_server(srv, scans, geoms, sparams, lanes)
+    warm_up_server(srv, scans, geoms, sparams, lanes, passes)
     identical = True
     sampler.start()
     for load in loads:
@@ -776,14 +786,20 @@ def serve_measure(n_scans, loads, storage, local, lanes=4):
     clocks = sampler.stop()
     info = srv.query()
     srv.close()
-    # back-to-back stream (all scans submitted at once): the throughput ceiling
-    srv = cbct.Server(use_graphs=True, concurrency=lanes)
-    warm_up_server(srv, scans, geoms, sparams, lanes)
-    t0 = time.perf_counter()
-    tickets = [srv.submit(g, sparams, y, o) for (key, g, y, gi), o in zip(scans, outs)]
-    res = [srv.wait(t) for t in tickets]
-    burst = time.perf_counter() - t0
-    srv.close()
+    # back-to-back stream (all scans submitted at once): the throughput ceiling,
+    # with and without step reuse
+    bursts = {}
+    for reuse in ([True, False] if reuse_steps else [False]):
+        srv = cbct.Server(use_graphs=True, concurrency=lanes, reuse_steps=reuse)
+        warm_up_server(srv, scans, geoms, sparams, lanes, 2 if reuse else 1)
+        t0 = time.perf_counter()
+        tickets = [srv.submit(g, sparams, y, o) for (key, g, y, gi), o in zip(scans, outs)]
+        res = [srv.wait(t) for t in tickets]
+        bursts[reuse] = time.perf_counter() - t0
+        srv.close()
+        for o, dgst in zip(outs, digests):
+            identical &= hashlib.sha1(o.numpy().tobytes()).hexdigest() == dgst
+    burst = bursts[reuse_steps]
     rms_srv = [float(np.sqrt(np.mean((o.numpy().reshape(g.vol_shape) - truths[gi]) ** 2)))
                for (key, g, y, gi), o in zip(scans, outs)]
     line = {"metric": "serving: scan latency p50/p99 (s) and scans/min, mixed 64-scan stream",
@@ -797,6 +813,9 @@ def serve_measure(n_scans, loads, storage, local, lanes=4):
             "sequential": {"scans_per_min": 60.0 * capacity, "total_s": seq_total,
                            "mean_service_s": float(np.mean(service))},
             "server_burst": {"scans_per_min": 60.0 * len(scans) / burst, "total_s": burst},
+            "server_burst_without_step_reuse": ({"scans_per_min": 60.0 * len(scans) / bursts[False],
+                                                 "total_s": bursts[False]} if reuse_steps else None),
+            "reuse_steps": bool(reuse_steps),
             "loads": results, "storage": storage, "scans": len(scans), "concurrency": lanes,
             "bit_identical_to_sequential": bool(identical) if storage == "f32" else None,
             "rms_error_vs_phantom": {"sequential_f32": float(np.mean(rms)), "server": float(np.mean(rms_srv)),
@@ -804,6 +823,7 @@ def serve_measure(n_scans, loads, storage, local, lanes=4):
                                                                         zip(rms_srv, rms)))},
             "server": {"slots": int(info.slots), "graphs_captured": int(info.graphs_captured),
                        "graph_failures": int(info.graph_failures), "evictions": int(info.evictions),
+                       "step_reuses": int(info.step_reuses),
                        "peak_arena_gb": info.peak_bytes_in_use / 1e9, "arena_gb": info.arena_bytes / 1e9},
             "clocks": clocks}
     return line

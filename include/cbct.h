@@ -326,7 +326,13 @@ cbct_status cbct_reconstruct_host(const cbct_geometry *geom, const float *h_sino
  * depend on the grid size, so a served scan equals the same scan
  * reconstructed directly, bit for bit. With use_graphs, the
  * first reconstruction in a slot is captured as a CUDA graph and every later
- * scan in that slot replays it (one launch per scan).
+ * scan in that slot replays it (one launch per scan). With reuse_steps, the
+ * per-level step sizes that a scan's power iterations find (they depend on
+ * the geometry and the parameters only, not on the data) are kept per
+ * (geometry, parameters) pair, and later scans of the pair run with those
+ * taus given instead of repeating the power iterations; the kernels are
+ * deterministic, so such a scan still equals the direct reconstruction bit
+ * for bit, and its statistics report the same tau and L.
  *
  * Host buffers must be page-locked (cudaHostAlloc / cudaHostRegister) and stay
  * valid, like the geometry, until the scan's cbct_server_wait returns. Slots
@@ -342,6 +348,7 @@ typedef struct {
     int use_graphs;       /* 1: capture each slot's reconstruction once and replay it */
     int concurrency;      /* reconstructions in flight at once, each on its own compute stream
                              with its TV solves on 1/concurrency of the GPU (0 or 1: one at a time) */
+    int reuse_steps;      /* 1: reuse each (geometry, parameters) pair's power-iteration taus */
 } cbct_server_config;
 
 typedef struct {
@@ -352,12 +359,14 @@ typedef struct {
     int32_t slot;           /* slot index it ran in */
     double t_submit, t_admit, t_done;  /* host seconds since server creation */
     double gpu_ms;          /* device time of the reconstruction (CUDA events) */
+    int32_t steps_reused;   /* 1: ran with the taus of an earlier scan of its geometry */
 } cbct_scan_result;
 
 typedef struct {
     size_t arena_bytes, bytes_in_use, peak_bytes_in_use;
     int32_t slots, busy_slots, graphs_captured, graph_failures;
     int64_t submitted, completed, evictions;
+    int64_t step_reuses;    /* scans that ran with reused taus */
 } cbct_server_info;
 
 cbct_status cbct_server_create(const cbct_server_config *cfg, cbct_server **out);

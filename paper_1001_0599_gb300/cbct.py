@@ -81,20 +81,22 @@ class ReconStats(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_resident", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("concurrency", ctypes.c_int)]
+                ("concurrency", ctypes.c_int), ("reuse_steps", ctypes.c_int)]
 
 
 class ScanResult(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("graph_replay", ctypes.c_int32),
                 ("recon_flags", ctypes.c_uint32), ("slot", ctypes.c_int32), ("t_submit", ctypes.c_double),
-                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("gpu_ms", ctypes.c_double)]
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("gpu_ms", ctypes.c_double),
+                ("steps_reused", ctypes.c_int32)]
 
 
 class ServerInfo(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_size_t), ("bytes_in_use", ctypes.c_size_t),
                 ("peak_bytes_in_use", ctypes.c_size_t), ("slots", ctypes.c_int32), ("busy_slots", ctypes.c_int32),
                 ("graphs_captured", ctypes.c_int32), ("graph_failures", ctypes.c_int32),
-                ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("evictions", ctypes.c_int64)]
+                ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("evictions", ctypes.c_int64),
+                ("step_reuses", ctypes.c_int64)]
 
 
 _lib = None
@@ -522,9 +524,10 @@ class Server:
     order, overlapping copies with computation (see include/cbct.h)."""
 
     def __init__(self, arena_bytes: int = 0, max_resident: int = 0, use_graphs: bool = True,
-                 concurrency: int = 1):
+                 concurrency: int = 1, reuse_steps: bool = False):
         L = load()
-        self.cfg = ServerConfig(int(arena_bytes), int(max_resident), 1 if use_graphs else 0, int(concurrency))
+        self.cfg = ServerConfig(int(arena_bytes), int(max_resident), 1 if use_graphs else 0, int(concurrency),
+                                1 if reuse_steps else 0)
         h = _P()
         _check(L.cbct_server_create(ctypes.byref(self.cfg), ctypes.byref(h)))
         self.handle = h.value

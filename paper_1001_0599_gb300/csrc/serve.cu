@@ -25,10 +25,20 @@
 // direct reconstruction bit for bit. With graphs enabled, a slot's first
 // reconstruction is captured (on a private stream) and instantiated; later
 // scans in the slot replay the graph with a single launch.
+//
+// Step reuse (config.reuse_steps): the step size tau = 1/L of each multigrid
+// level comes from power iterations on kappa P^T P, which depend on the
+// geometry and the schedule only, never on a scan's data. The first scan of a
+// (geometry, parameters) pair runs them and its statistics record tau and L;
+// later scans of the pair run with those taus given. The kernels are
+// deterministic, so the given taus are the very doubles the power iterations
+// would produce again, and a scan that reuses them still equals the direct
+// reconstruction bit for bit (its statistics report the same tau and L).
 #include "cbct_internal.cuh"
 
 #include <algorithm>
 #include <chrono>
+#include <cstddef>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -50,6 +60,10 @@ using namespace cbct;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kPinnedHeads = 64;   // statistics heads copied out at once for step reuse
+// leading fields of cbct_recon_stats that step reuse reads back: tau, lipschitz,
+// n_iters, flags, status
+constexpr size_t kStatsHead = offsetof(cbct_recon_stats, n_steps);
 size_t round_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // First-fit allocator over [0, size) with coalescing on free.
@@ -102,7 +116,9 @@ class Arena {
 struct Slot {
     const cbct_geometry *geom = nullptr;
     uint64_t geom_serial = 0;   // geometries are matched by serial, never by address
-    cbct_recon_params params{};
+    cbct_recon_params params{};       // as submitted (slots are matched on these)
+    cbct_recon_params run{};          // as launched: with reused taus filled in
+    bool run_reuses_steps = false;    // the captured graph (if any) was made from such params
     size_t off = 0, bytes = 0;
     float *sino = nullptr, *vol = nullptr;
     void *ws = nullptr;
@@ -127,6 +143,10 @@ struct Job {
     int slot = -1;
     int lane = 0;
     double cost = 0.0;   // work estimate: rays x in-plane voxels along a ray
+    cbct_recon_params run{};   // params as launched (reused taus filled in)
+    int step_entry = -1;       // entry of the step cache this scan reads or fills
+    bool steps_reused = false; // runs with the entry's taus instead of power iterations
+    int pin = -1;              // pinned statistics head this scan fills the entry from
     cudaEvent_t ev_in = nullptr, ev_start = nullptr, ev_stop = nullptr, ev_out = nullptr;
     bool done = false;
 };
@@ -135,6 +155,24 @@ bool same_params(const cbct_recon_params &a, const cbct_recon_params &b)
 {
     return std::memcmp(&a, &b, sizeof(a)) == 0;
 }
+
+// Does the reconstruction run power iterations on some level (tau not given)?
+bool needs_power(const cbct_recon_params &p)
+{
+    for (int l = 0; l < p.n_levels && l < CBCT_MAX_LEVELS; l++)
+        if (!(p.tau[l] > 0)) return true;
+    return false;
+}
+
+// Step sizes learned for one (geometry, parameters) pair.
+struct StepEntry {
+    uint64_t geom_serial = 0;
+    cbct_recon_params params{};
+    bool ready = false;     // tau and lipschitz hold the pair's values
+    bool pending = false;   // a scan in flight will fill them
+    double tau[CBCT_MAX_LEVELS] = {};
+    double lipschitz[CBCT_MAX_LEVELS] = {};
+};
 
 size_t slot_bytes(const cbct_geometry *G, const cbct_recon_params *p, size_t *ws_bytes)
 {
@@ -167,9 +205,12 @@ struct cbct_server {
     std::deque<std::shared_ptr<Job>> inflight;    // issued, not completed
     std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;
     std::vector<Slot> slots;
+    std::vector<StepEntry> steps;      // step cache (reuse_steps)
+    char *pinned = nullptr;            // kPinnedHeads statistics heads, page-locked
+    std::vector<int> pin_free;
     uint64_t next_ticket = 1, use_clock = 0;
     bool stop = false;
-    int64_t submitted = 0, completed = 0, evictions = 0;
+    int64_t submitted = 0, completed = 0, evictions = 0, step_reuses = 0;
     int graphs_captured = 0, graph_failures = 0;
     std::thread sched, compl_;
 
@@ -237,6 +278,8 @@ int acquire_slot(cbct_server *S, const Job &j)
     sl.geom = j.geom;
     sl.geom_serial = geometry_serial(j.geom);
     sl.params = j.params;
+    sl.run = j.params;
+    sl.run_reuses_steps = false;
     sl.off = off;
     sl.bytes = need;
     sl.nray = (size_t)d->n_views * d->nv * d->nu;
@@ -258,7 +301,7 @@ cbct_status enqueue_recon(Slot &sl, cudaStream_t s)
 {
     if (cudaMemsetAsync(sl.vol, 0, sizeof(float) * sl.nvox, s) != cudaSuccess)
         return report_error(CBCT_ERR_CUDA, "cudaMemsetAsync of the slot volume failed");
-    return cbct_reconstruct(sl.geom, sl.sino, sl.vol, &sl.params, sl.ws, sl.ws_bytes, sl.stats, s);
+    return cbct_reconstruct(sl.geom, sl.sino, sl.vol, &sl.run, sl.ws, sl.ws_bytes, sl.stats, s);
 }
 
 // Capture the slot's reconstruction once; false leaves the slot on direct launches.
@@ -287,6 +330,66 @@ bool capture_slot(cbct_server *S, Slot &sl)
     return true;
 }
 
+// Step reuse: give the job the cached taus of its (geometry, parameters)
+// pair, or make it the scan that fills them (one filler at a time per pair).
+void plan_steps(cbct_server *S, Job &j)
+{
+    j.run = j.params;
+    if (!S->cfg.reuse_steps || !needs_power(j.params)) return;
+    const uint64_t serial = geometry_serial(j.geom);
+    int e = -1;
+    for (int i = 0; i < (int)S->steps.size(); i++)
+        if (S->steps[i].geom_serial == serial && same_params(S->steps[i].params, j.params)) {
+            e = i;
+            break;
+        }
+    if (e >= 0 && S->steps[e].ready) {
+        for (int l = 0; l < j.params.n_levels && l < CBCT_MAX_LEVELS; l++)
+            if (!(j.params.tau[l] > 0)) j.run.tau[l] = S->steps[e].tau[l];
+        j.step_entry = e;
+        j.steps_reused = true;
+        return;
+    }
+    if ((e >= 0 && S->steps[e].pending) || S->pin_free.empty()) return;
+    if (e < 0) {
+        StepEntry se;
+        se.geom_serial = serial;
+        se.params = j.params;
+        S->steps.push_back(se);
+        e = (int)S->steps.size() - 1;
+    }
+    S->steps[e].pending = true;
+    j.step_entry = e;
+    j.pin = S->pin_free.back();
+    S->pin_free.pop_back();
+}
+
+// After the job's copy-out: a filler stores the taus its power iterations
+// found (if the reconstruction succeeded); a reuser reports the cached L in
+// its statistics, as the power iterations would have.
+void finish_steps(cbct_server *S, Job &j, bool ok)
+{
+    if (j.step_entry < 0) return;
+    StepEntry &se = S->steps[j.step_entry];
+    if (j.pin >= 0) {
+        cbct_recon_stats head;
+        std::memcpy(&head, S->pinned + (size_t)j.pin * kStatsHead, kStatsHead);
+        if (ok && head.status == CBCT_OK) {
+            for (int l = 0; l < CBCT_MAX_LEVELS; l++) {
+                se.tau[l] = head.tau[l];
+                se.lipschitz[l] = head.lipschitz[l];
+            }
+            se.ready = true;
+        }
+        se.pending = false;
+        S->pin_free.push_back(j.pin);
+        j.pin = -1;
+    }
+    if (j.steps_reused && ok && j.h_stats)
+        for (int l = 0; l < j.params.n_levels && l < CBCT_MAX_LEVELS; l++)
+            if (!(j.params.tau[l] > 0)) j.h_stats->lipschitz[l] = se.lipschitz[l];
+}
+
 void fail_job(cbct_server *S, const std::shared_ptr<Job> &j, cbct_status st)
 {
     j->res.status = st;
@@ -309,6 +412,7 @@ void scheduler_loop(cbct_server *S)
             continue;
         }
         std::shared_ptr<Job> j = S->queue.front();
+        if (j->step_entry < 0) plan_steps(S, *j);
         const int si = acquire_slot(S, *j);
         if (si < 0) {  // every slot busy: wait for a completion
             S->cv_sched.wait(lk);
@@ -333,6 +437,14 @@ void scheduler_loop(cbct_server *S)
         }
         S->lane_work[lane] += j->cost;
         cudaStream_t s_comp = S->s_comp[lane], s_out = S->s_out[lane];
+        if (!same_params(sl.run, j->run) || sl.run_reuses_steps != j->steps_reused) {
+            // the slot's graph was made from other launch parameters
+            if (sl.graph) cudaGraphExecDestroy(sl.graph);
+            sl.graph = nullptr;
+            sl.graph_failed = false;
+            sl.run = j->run;
+            sl.run_reuses_steps = j->steps_reused;
+        }
         // issue (the lock is held: slots and the arena are not touched elsewhere
         // while this runs, and the enqueue calls do not block)
         cbct_status st = CBCT_OK;
@@ -364,6 +476,8 @@ void scheduler_loop(cbct_server *S)
                  cudaSuccess &&
              (!j->h_stats || cudaMemcpyAsync(j->h_stats, sl.stats, sizeof(cbct_recon_stats),
                                              cudaMemcpyDeviceToHost, s_out) == cudaSuccess) &&
+             (j->pin < 0 || cudaMemcpyAsync(S->pinned + (size_t)j->pin * kStatsHead, sl.stats, kStatsHead,
+                                            cudaMemcpyDeviceToHost, s_out) == cudaSuccess) &&
              cudaEventRecord(j->ev_out, s_out) == cudaSuccess;
         if (!ok) {
             // work may be partially enqueued: let it drain before the slot is reused
@@ -373,10 +487,12 @@ void scheduler_loop(cbct_server *S)
             cudaStreamSynchronize(s_out);
             S->lane_work[lane] -= j->cost;
             sl.busy = false;
+            finish_steps(S, *j, false);
             fail_job(S, j, st != CBCT_OK ? st : CBCT_ERR_CUDA);
             S->cv_done.notify_all();
             continue;
         }
+        if (j->steps_reused) S->step_reuses++;
         S->inflight.push_back(j);
         S->cv_done.notify_all();
     }
@@ -390,6 +506,8 @@ void complete_job(cbct_server *S, const std::shared_ptr<Job> &j, cudaError_t e)
     j->res.gpu_ms = ms;
     j->res.status = e == cudaSuccess ? CBCT_OK : CBCT_ERR_CUDA;
     if (e == cudaSuccess && j->h_stats) j->res.recon_flags = j->h_stats->flags;
+    j->res.steps_reused = j->steps_reused ? 1 : 0;
+    finish_steps(S, *j, e == cudaSuccess);
     j->res.t_done = S->now();
     j->done = true;
     S->lane_work[j->lane] -= j->cost;
@@ -471,6 +589,14 @@ extern "C" cbct_status cbct_server_create(const cbct_server_config *cfg, cbct_se
         return report_error(CBCT_ERR_OUT_OF_MEMORY, "cudaMalloc of the serving arena failed");
     }
     S->arena = std::make_unique<Arena>(c.arena_bytes);
+    if (c.reuse_steps) {
+        if (cudaHostAlloc((void **)&S->pinned, kStatsHead * kPinnedHeads, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(S->base);
+            return report_error(CBCT_ERR_OUT_OF_MEMORY, "cudaHostAlloc of the step-reuse buffer failed");
+        }
+        for (int i = kPinnedHeads - 1; i >= 0; i--) S->pin_free.push_back(i);
+    }
     S->lanes = c.concurrency > 1 ? c.concurrency : 1;
     std::vector<cudaStream_t *> streams = {&S->s_in, &S->s_cap};
     for (int l = 0; l < S->lanes; l++) {
@@ -481,6 +607,7 @@ extern "C" cbct_status cbct_server_create(const cbct_server_config *cfg, cbct_se
         if (cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) != cudaSuccess) {
             for (cudaStream_t *t : streams)
                 if (*t) cudaStreamDestroy(*t);
+            if (S->pinned) cudaFreeHost(S->pinned);
             cudaFree(S->base);
             return report_error(CBCT_ERR_CUDA, "cudaStreamCreate failed");
         }
@@ -522,6 +649,7 @@ extern "C" void cbct_server_destroy(cbct_server *S)
         if (S->s_comp[l]) cudaStreamDestroy(S->s_comp[l]);
         if (S->s_out[l]) cudaStreamDestroy(S->s_out[l]);
     }
+    if (S->pinned) cudaFreeHost(S->pinned);
     cudaFree(S->base);
     delete S;
 }
@@ -615,5 +743,6 @@ extern "C" cbct_status cbct_server_query(cbct_server *S, cbct_server_info *info)
     info->submitted = S->submitted;
     info->completed = S->completed;
     info->evictions = S->evictions;
+    info->step_reuses = S->step_reuses;
     return CBCT_OK;
 }

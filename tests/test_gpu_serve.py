@@ -238,3 +238,36 @@ def test_served_scan_matches_oracle(lib, orc):
         ref = orc.reconstruct(og, f32(y), wl.lam, (6,), p, power_iters=20, replay=sched)
         assert st.tau[0] == pytest.approx(ref.taus[0], rel=1e-5)
         assert rel_l2(v.astype(np.float64), ref.f) < TOL_RECON
+
+
+@pytest.mark.parametrize("lanes", [1, 3])
+def test_reused_steps_equal_direct_reconstruction(lib, lanes):
+    # with reuse_steps, the first scan of each (geometry, parameters) pair runs
+    # the power iterations and later scans of the pair take its taus: the
+    # kernels are deterministic, so every scan still equals its direct
+    # reconstruction bit for bit, with the same tau and L in its statistics
+    import torch
+    scans = _scans(lib, ["small", "odd", "tall"], 3, seed=5)
+    ref = [_direct(lib, g, p, s) for _, g, p, s in scans]
+    for graphs in (True, False):
+        srv = lib.Server(use_graphs=graphs, concurrency=lanes, reuse_steps=True)
+        got, res = [], []
+        for batch in (scans[:3], scans[3:]):   # the second batch finds every pair's taus
+            outs, tickets = [], []
+            for name, g, params, h_sino in batch:
+                h_vol = torch.empty(g.vol_shape).pin_memory()
+                h_st = lib.pinned_stats_buffer()
+                tickets.append(srv.submit(g, params, h_sino, h_vol, h_st))
+                outs.append((h_vol, h_st))
+            res += [srv.wait(t) for t in tickets]
+            got += [(v.numpy().copy(), lib.read_host_stats(s)) for v, s in outs]
+        info = srv.query()
+        srv.close()
+        assert [r.steps_reused for r in res] == [0] * 3 + [1] * 6
+        assert info.step_reuses == 6 and info.completed == len(scans)
+        for (v, st), (rv, rst), r in zip(got, ref, res):
+            assert r.status == 0
+            assert np.array_equal(v, rv)
+            assert st.n_iters == rst.n_iters and st.flags == rst.flags
+            assert list(st.tau[:2]) == list(rst.tau[:2])
+            assert list(st.lipschitz[:2]) == list(rst.lipschitz[:2])
