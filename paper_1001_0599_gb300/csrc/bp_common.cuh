@@ -6,6 +6,8 @@
 
 #include "cbct_internal.cuh"
 
+#include <utility>
+
 namespace cbct {
 
 constexpr int BP_G = 4;   // a warp owns a BP_G x BP_G group of voxel columns
@@ -15,6 +17,29 @@ struct Box {
 };
 
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.f, x); }
+
+// One row T of a z tent window starting at shared address pa: the weight
+// 1 - sc |dq + T|, clamped at zero from row CLAMP_FROM on (the rows where it
+// can be negative), times the row, into one of two interleaved sums.
+template <int CLAMP_FROM, int T>
+__device__ __forceinline__ void tent_row(uint32_t pa, float dq, float sc, float &s, float &s2)
+{
+    float w = __fmaf_rn(-sc, fabsf(dq + (float)T), 1.f);
+    if (T >= CLAMP_FROM) w = fmaxf(w, 0.f);
+    const float v = lds_off<4 * T>(pa);
+    if (T & 1)
+        s2 = __fmaf_rn(w, v, s2);
+    else
+        s = __fmaf_rn(w, v, s);
+}
+
+// rows 0 .. W-1; the weight is clamped at zero from row CLAMP_FROM on
+template <int CLAMP_FROM, int... T>
+__device__ __forceinline__ void tent_rows_imm(uint32_t pa, float dq, float sc, float &s, float &s2,
+                                              std::integer_sequence<int, T...>)
+{
+    (tent_row<CLAMP_FROM, T>(pa, dq, sc, s, s2), ...);
+}
 
 // Does sample j of the line touch the BP_G x BP_G group of columns at (A, B)?
 // Its cell (floor of the sample's voxel coordinates) must lie in

@@ -113,14 +113,17 @@ __device__ __forceinline__ long long bs_start(long long b, long long U, long lon
 // into the staged rows [qlo, qhi] (inactive on a correctly staged patch:
 // a bounds guard; rows beyond the detector hold zeros).
 template <int W, bool CLAMP>
-__device__ __forceinline__ float bs_tent(const float *patch, int col, float q, float m, float sc, float qlo,
-                                         float qhi)
+__device__ __forceinline__ float bs_tent(const float *patch, uint32_t pbase, int col, float q, float m, float sc,
+                                         float qlo, float qhi)
 {
     const float qm = CLAMP ? fminf(fmaxf(q - m, qlo), qhi) : q - m;
     const float tb = __fadd_ru(qm, BS_ROUND);   // BS_ROUND + ceil(qm), exact for |qm| < 2^22
     const int base = col + (__float_as_int(tb) - BS_ROUND_BITS);
     const float dq = (tb - BS_ROUND) - q;
     float s = 0.f, s2 = 0.f;
+#if CBCT_LDS_IMM
+    tent_rows_imm<W - 2>(pbase + 4u * (uint32_t)base, dq, sc, s, s2, std::make_integer_sequence<int, W>{});
+#else
 #pragma unroll
     for (int t = 0; t < W; ++t) {
         float w = __fmaf_rn(-sc, fabsf(dq + (float)t), 1.f);
@@ -130,6 +133,7 @@ __device__ __forceinline__ float bs_tent(const float *patch, int col, float q, f
         else
             s = __fmaf_rn(w, patch[base + t], s);
     }
+#endif
     return s + s2;
 }
 
@@ -179,6 +183,7 @@ bs_kernel(const BsArgs a)
     constexpr int TVOX = BS_TX * BS_TY * TZ;
     extern __shared__ float patch[];
     __shared__ BsEntry s_ent[BS_WARPS][BS_NENT];
+    const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(patch);
     __shared__ int s_box[6];
     __shared__ double red[32];
     __shared__ int s_last;
@@ -376,12 +381,12 @@ bs_kernel(const BsArgs a)
                             if (cell & BS_SHORT) {
 #pragma unroll
                                 for (int zc = 0; zc < ZC; ++zc)
-                                    sv[zc] = bs_tent<NR - 1, true>(patch, col, __fmaf_rn(ccz[zc], m, d.cv), m, sc, qlo,
+                                    sv[zc] = bs_tent<NR - 1, true>(patch, pbase, col, __fmaf_rn(ccz[zc], m, d.cv), m, sc, qlo,
                                                                    qhi_short);
                             } else {
 #pragma unroll
                                 for (int zc = 0; zc < ZC; ++zc)
-                                    sv[zc] = bs_tent<NR, true>(patch, col, __fmaf_rn(ccz[zc], m, d.cv), m, sc, qlo,
+                                    sv[zc] = bs_tent<NR, true>(patch, pbase, col, __fmaf_rn(ccz[zc], m, d.cv), m, sc, qlo,
                                                                qhi_long);
                             }
                             const float4 wq = *reinterpret_cast<const float4 *>(&s_ent[warp][e].w00);

@@ -52,6 +52,21 @@ struct DetGeom {
 
 // Continuous voxel coordinates of sample j of a ray line (shared by the
 // projector and its transpose so both see identical sample positions).
+#ifndef CBCT_LDS_IMM
+#define CBCT_LDS_IMM 1   // transpose tent rows read with immediate offsets (build-time tuning: 0 or 1)
+#endif
+
+// Shared-memory load at a 32-bit shared-window address plus a compile-time
+// byte offset carried in the load's immediate field: a run of consecutive
+// rows then costs one address computation, not one per row.
+template <int OFF>
+__device__ __forceinline__ float lds_off(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
+    return v;
+}
+
 __device__ __forceinline__ void sample_xy(const VolGeom &g, const RayCol &rc, int j, float &fx,
                                           float &fy)
 {
