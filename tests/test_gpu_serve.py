@@ -271,3 +271,49 @@ def test_reused_steps_equal_direct_reconstruction(lib, lanes):
             assert st.n_iters == rst.n_iters and st.flags == rst.flags
             assert list(st.tau[:2]) == list(rst.tau[:2])
             assert list(st.lipschitz[:2]) == list(rst.lipschitz[:2])
+
+
+def test_serving_mix_shapes_equal_direct_reconstruction(lib):
+    # two shapes of the serving mix at full size (128^3 at 2 mm with 20 views on
+    # the 256x192 detector, 192x192x128 with 40 views on the 512x384 one), the
+    # mix's 50-iteration 20/15/15 schedule, 2 lanes with step reuse: every
+    # served scan, including those that reuse their shape's taus, equals its
+    # direct reconstruction bit for bit
+    import torch
+    from paper_1001_0599_gb300 import synthetic
+    shapes = [(128, 128, 128, 2.0, 2.0, 2.0, 256, 192, 1.56, 1.56, 20),
+              (192, 192, 128, 4.0 / 3.0, 4.0 / 3.0, 1.0, 512, 384, 0.78, 0.78, 40)]
+    tv = lib.TvParams.paper(eps_tv=1e-5)
+    params = lib.make_recon_params(0.05, (20, 15, 15), tv, power_iters=20, clamp=True, power_iters_fine=4)
+    scans = []
+    for k, (nx, ny, nz, dx, dy, dz, nu, nv, du, dv, views) in enumerate(shapes):
+        wl = synthetic.Workload(f"mix{k}", nx, ny, nz, dx, dy, dz, nu, nv, du, dv, views, photons=5e4,
+                                phantom="head_neck", phantom_seed=3, noise_seed=10, lam=0.05, iters=(20, 15, 15))
+        g = lib.geometry_from_workload(wl)
+        truth = synthetic.voxelise(synthetic.make_phantom(wl), nx, ny, nz, dx, dy, dz).astype(np.float32)
+        p = torch.empty(g.sino_shape, device="cuda")
+        lib.cbct_forward_project(g, torch.from_numpy(truth).cuda(), p)
+        for rep in range(2):
+            gen = torch.Generator(device="cuda").manual_seed(100 * k + rep)
+            counts = torch.poisson(wl.photons * torch.exp(-p), generator=gen)
+            y = torch.log(wl.photons / counts.clamp_min(1.0)).float()
+            scans.append((wl.name, g, params, y.cpu().contiguous().pin_memory()))
+    ref = [_direct(lib, g, p, s) for _, g, p, s in scans]
+    srv = lib.Server(use_graphs=True, concurrency=2, reuse_steps=True)
+    got, res = [], []
+    for batch in (scans[0::2], scans[1::2]):   # the second scan of each shape reuses the first one's taus
+        outs, tickets = [], []
+        for name, g, p, h_sino in batch:
+            h_vol = torch.empty(g.vol_shape).pin_memory()
+            h_st = lib.pinned_stats_buffer()
+            tickets.append(srv.submit(g, p, h_sino, h_vol, h_st))
+            outs.append((h_vol, h_st))
+        res += [srv.wait(t) for t in tickets]
+        got += [(v.numpy().copy(), lib.read_host_stats(s)) for v, s in outs]
+    srv.close()
+    ref = [ref[i] for i in (0, 2, 1, 3)]
+    assert [r.steps_reused for r in res] == [0, 0, 1, 1]
+    for (v, st), (rv, rst), r in zip(got, ref, res):
+        assert r.status == 0
+        assert np.array_equal(v, rv)
+        assert list(st.tau[:3]) == list(rst.tau[:3]) and list(st.lipschitz[:3]) == list(rst.lipschitz[:3])
