@@ -44,6 +44,10 @@ constexpr int BS_THREADS = 32 * BS_WARPS;
 #define CBCT_BS_NENT 64                   // list entries per warp and batch (build-time tuning)
 #endif
 constexpr int BS_NENT = CBCT_BS_NENT;
+#ifndef CBCT_BS_NENT_BIG
+#define CBCT_BS_NENT_BIG 128              // larger batch of the 4-chunk variants, taken where it costs no occupancy (0: never)
+#endif
+constexpr int BS_NENT_BIG = CBCT_BS_NENT_BIG > 0 ? CBCT_BS_NENT_BIG : CBCT_BS_NENT;
 constexpr float BS_ROUND = 12582912.f;     // 1.5 * 2^23: x + BS_ROUND rounds x to an integer
 constexpr int BS_ROUND_BITS = 0x4B400000;  // bit pattern of BS_ROUND
 constexpr int BS_SHORT = 256;              // entry flag: the tent fits the shorter window
@@ -174,15 +178,16 @@ __device__ __forceinline__ int bs_local(int warp, int ia, int ib, int zlocal, in
 }
 
 // MODE 0: out = P^T sino; MODE 1: out = f - scale P^T sino; MODE 2: out =
-// kappa P^T sino with the tile's sum of squares in partials[tile].
-template <int MODE, int NR, int ZC>
+// kappa P^T sino with the tile's sum of squares in partials[tile]. NENT: list
+// entries per warp and batch.
+template <int MODE, int NR, int ZC, int NENT>
 __global__ void __launch_bounds__(BS_THREADS, ZC >= 4 ? CBCT_BS_ZC4_BLOCKS : 5)
 bs_kernel(const BsArgs a)
 {
     constexpr int TZ = 32 * ZC;
     constexpr int TVOX = BS_TX * BS_TY * TZ;
     extern __shared__ float patch[];
-    __shared__ BsEntry s_ent[BS_WARPS][BS_NENT];
+    __shared__ BsEntry s_ent[BS_WARPS][NENT];
     const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(patch);
     __shared__ int s_box[6];
     __shared__ double red[32];
@@ -341,8 +346,8 @@ bs_kernel(const BsArgs a)
                     const int total = __shfl_sync(0xffffffffu, incl, 31);
                     const int first = incl - cnt;
                     const int col_off = (iu - iu0) * hp - s0;
-                    for (int b0 = 0; b0 < total; b0 += BS_NENT) {
-                        const int lo = max(first, b0), hi = min(first + cnt, b0 + BS_NENT);
+                    for (int b0 = 0; b0 < total; b0 += NENT) {
+                        const int lo = max(first, b0), hi = min(first + cnt, b0 + NENT);
                         // the line is read again per batch so that it holds no registers
                         // while the batch is processed
                         const RayCol rc2 = lo < hi ? ld_raycol(g.cols + (size_t)view * d.nu + iu) : RayCol{};
@@ -371,7 +376,7 @@ bs_kernel(const BsArgs a)
                             s_ent[warp][e - b0] = en;
                         }
                         __syncwarp();
-                        const int nb = min(BS_NENT, total - b0);
+                        const int nb = min(NENT, total - b0);
                         for (int e = 0; e < nb; ++e) {
                             // the entry's geometry first; its weights only once the tents are done
                             const float4 h = *reinterpret_cast<const float4 *>(&s_ent[warp][e]);
@@ -455,36 +460,39 @@ bs_kernel(const BsArgs a)
     }
 }
 
-template <int MODE, int NR, int ZC>
+template <int MODE, int NR, int ZC, int NENT>
 static cudaError_t bs_prepare(size_t smem, int *occ)
 {
-    cudaError_t e = cudaFuncSetAttribute(bs_kernel<MODE, NR, ZC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(bs_kernel<MODE, NR, ZC, NENT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(bs_kernel<MODE, NR, ZC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(bs_kernel<MODE, NR, ZC, NENT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bs_kernel<MODE, NR, ZC>, BS_THREADS, smem);
+    if (occ)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bs_kernel<MODE, NR, ZC, NENT>, BS_THREADS, smem);
     return cudaSuccess;
 }
 
-template <int MODE, int NR, int ZC>
+template <int MODE, int NR, int ZC, int NENT>
 static cudaError_t bs_go(int grid, size_t smem, cudaStream_t s, const BsArgs &a, int *occ)
 {
-    cudaError_t e = bs_prepare<MODE, NR, ZC>(smem, occ);
+    cudaError_t e = bs_prepare<MODE, NR, ZC, NENT>(smem, occ);
     if (e != cudaSuccess || occ) return e;
-    bs_kernel<MODE, NR, ZC><<<grid, BS_THREADS, smem, s>>>(a);
+    bs_kernel<MODE, NR, ZC, NENT><<<grid, BS_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+// nent: list batch (BS_NENT, or BS_NENT_BIG for the 4-chunk variants)
 template <int MODE>
-cudaError_t bs_dispatch(int nr, int zc, int grid, size_t smem, cudaStream_t s, const BsArgs &a, int *occ)
+cudaError_t bs_dispatch(int nr, int zc, int nent, int grid, size_t smem, cudaStream_t s, const BsArgs &a, int *occ)
 {
 #define CBCT_BS_CASE(NRV)                                                                           \
     case NRV:                                                                                       \
-        if (zc == 1) return bs_go<MODE, NRV, 1>(grid, smem, s, a, occ);                             \
-        if (zc == 2) return bs_go<MODE, NRV, 2>(grid, smem, s, a, occ);                             \
-        return bs_go<MODE, NRV, 4>(grid, smem, s, a, occ);
+        if (zc == 1) return bs_go<MODE, NRV, 1, BS_NENT>(grid, smem, s, a, occ);                    \
+        if (zc == 2) return bs_go<MODE, NRV, 2, BS_NENT>(grid, smem, s, a, occ);                    \
+        if (nent == BS_NENT_BIG) return bs_go<MODE, NRV, 4, BS_NENT_BIG>(grid, smem, s, a, occ);    \
+        return bs_go<MODE, NRV, 4, BS_NENT>(grid, smem, s, a, occ);
     switch (nr) {
         CBCT_BS_CASE(4)
         CBCT_BS_CASE(5)
@@ -497,7 +505,7 @@ cudaError_t bs_dispatch(int nr, int zc, int grid, size_t smem, cudaStream_t s, c
 }
 
 #define CBCT_BS_SIG(MODE) \
-    cudaError_t bs_dispatch<MODE>(int, int, int, size_t, cudaStream_t, const BsArgs &, int *)
+    cudaError_t bs_dispatch<MODE>(int, int, int, int, size_t, cudaStream_t, const BsArgs &, int *)
 #if BS_UNIT == 0
 extern template CBCT_BS_SIG(1);
 extern template CBCT_BS_SIG(2);
@@ -561,12 +569,39 @@ static int bs_sm_count(int dev)
     return n > 0 ? n : 1;
 }
 
-// Resident blocks of the grid's variant (per device, geometry shape and mode):
-// the stream-K grid.
-static int bs_resident_blocks(const VolGeom &v, const DetGeom &d, int mode)
+static int bs_occupancy(const VolGeom &v, const DetGeom &d, int mode, int nent)
+{
+    int occ = 0;
+    BsArgs a{};
+    const size_t smem = (size_t)v.bs_cap * sizeof(float);
+    cudaError_t e;
+    if (mode == 0)
+        e = bs_dispatch<0>(bs_nr(v, d), bs_zc(v), nent, 1, smem, 0, a, &occ);
+    else if (mode == 1)
+        e = bs_dispatch<1>(bs_nr(v, d), bs_zc(v), nent, 1, smem, 0, a, &occ);
+    else
+        e = bs_dispatch<2>(bs_nr(v, d), bs_zc(v), nent, 1, smem, 0, a, &occ);
+    if (e != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 0;
+    }
+    return occ;
+}
+
+// Launch plan of the grid's variant (per device, geometry shape and mode):
+// the list batch -- the larger one where it leaves as many resident blocks
+// per SM as the smaller one (measured: cubic finest grid 7.39 -> 7.15 ms with
+// both at 4 blocks per SM; where the larger batch costs a block per SM, the
+// paper finest grid ran 3.89 -> 4.28 ms) -- and the stream-K grid, its
+// resident blocks.
+struct BsPlan {
+    int blocks, nent;
+};
+
+static BsPlan bs_plan(const VolGeom &v, const DetGeom &d, int mode)
 {
     static std::mutex mu;
-    static std::vector<std::pair<std::array<int, 8>, int>> cache;
+    static std::vector<std::pair<std::array<int, 8>, BsPlan>> cache;
     int dev = 0;
     cudaGetDevice(&dev);
     const std::array<int, 8> key{dev, v.nx, v.ny, v.nz, d.nu, d.nv, v.bs_cap, mode};
@@ -575,30 +610,24 @@ static int bs_resident_blocks(const VolGeom &v, const DetGeom &d, int mode)
         for (const auto &kv : cache)
             if (kv.first == key) return kv.second;
     }
-    int occ = 0;
-    BsArgs a{};
-    const size_t smem = (size_t)v.bs_cap * sizeof(float);
-    cudaError_t e;
-    if (mode == 0)
-        e = bs_dispatch<0>(bs_nr(v, d), bs_zc(v), 1, smem, 0, a, &occ);
-    else if (mode == 1)
-        e = bs_dispatch<1>(bs_nr(v, d), bs_zc(v), 1, smem, 0, a, &occ);
-    else
-        e = bs_dispatch<2>(bs_nr(v, d), bs_zc(v), 1, smem, 0, a, &occ);
-    if (e != cudaSuccess || occ < 1) {
-        cudaGetLastError();
-        occ = 1;
+    int nent = BS_NENT, occ = bs_occupancy(v, d, mode, BS_NENT);
+    if (BS_NENT_BIG != BS_NENT && bs_zc(v) == 4) {
+        const int occ_big = bs_occupancy(v, d, mode, BS_NENT_BIG);
+        if (occ_big >= occ && occ_big > 0) {
+            nent = BS_NENT_BIG;
+            occ = occ_big;
+        }
     }
-    const int blocks = occ * bs_sm_count(dev);
+    const BsPlan plan{std::max(occ, 1) * bs_sm_count(dev), nent};
     std::lock_guard<std::mutex> lk(mu);
-    cache.emplace_back(key, blocks);
-    return blocks;
+    cache.emplace_back(key, plan);
+    return plan;
 }
 
 static int bs_grid(const VolGeom &v, const DetGeom &d, int mode)
 {
     const long long units = (long long)bs_tiles(v) * d.n_views;
-    return (int)std::min<long long>(bs_resident_blocks(v, d, mode), units);
+    return (int)std::min<long long>(bs_plan(v, d, mode).blocks, units);
 }
 
 // scratch floats of a stream-K launch: two tile partials per block
@@ -643,9 +672,10 @@ cudaError_t launch_bs(const VolGeom &v, const DetGeom &d, const void *sino, int 
         if (e != cudaSuccess) return e;
     }
     const size_t smem = (size_t)v.bs_cap * sizeof(float);
-    if (mode == 0) return bs_dispatch<0>(a.pad, zc, grid, smem, s, a, nullptr);
-    if (mode == 1) return bs_dispatch<1>(a.pad, zc, grid, smem, s, a, nullptr);
-    return bs_dispatch<2>(a.pad, zc, grid, smem, s, a, nullptr);
+    const int nent = bs_plan(v, d, mode).nent;
+    if (mode == 0) return bs_dispatch<0>(a.pad, zc, nent, grid, smem, s, a, nullptr);
+    if (mode == 1) return bs_dispatch<1>(a.pad, zc, nent, grid, smem, s, a, nullptr);
+    return bs_dispatch<2>(a.pad, zc, nent, grid, smem, s, a, nullptr);
 }
 
 #endif // BS_UNIT == 0
