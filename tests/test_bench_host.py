@@ -103,3 +103,22 @@ def test_schedule_from_reconstruction_statistics(bench):
     assert [lv["power"] for lv in sched["levels"]] == [20, 4, 4]
     assert [len(lv["fbs"]) for lv in sched["levels"]] == [40, 30, 30]
     assert sched["levels"][2]["fbs"][0] == {"n_inner": 2, "backtracks": 2}
+
+
+def test_serve_summary_reports_step_reuse(bench):
+    # the default line's serve block carries both back-to-back rates when the
+    # server reused step sizes, and a null second rate when it did not
+    load = {"load": 0.8, "p50_s": 0.2, "p99_s": 1.0, "scans_per_min": 200.0, "sequential_p50_s": 0.5,
+            "sequential_p99_s": 2.5, "gpu_s_per_scan": 0.3, "graph_replays": 32}
+    res = {"scans": 32, "loads": [load], "sequential": {"scans_per_min": 218.0},
+           "server_burst": {"scans_per_min": 412.0},
+           "server_burst_without_step_reuse": {"scans_per_min": 286.0}, "reuse_steps": True,
+           "bit_identical_to_sequential": True, "concurrency": 4, "config": {"workload": "mix"}, "clocks": {}}
+    out = bench.serve_summary(res)
+    assert out["server_burst_scans_per_min"] == 412.0
+    assert out["server_burst_without_step_reuse_scans_per_min"] == 286.0
+    assert out["reuse_steps"] is True and out["loads"][0]["p99_s"] == 1.0
+    assert "gpu_s_per_scan" not in out["loads"][0]
+    res.update(server_burst_without_step_reuse=None, reuse_steps=False)
+    out = bench.serve_summary(res)
+    assert out["server_burst_without_step_reuse_scans_per_min"] is None and out["reuse_steps"] is False
